@@ -1,0 +1,321 @@
+"""Seeded synthetic task streams: the inputs both sides of every check consume.
+
+This module only *describes* work. It draws the random initial buffer contents,
+chooses which task reads and writes which buffer range, and (for the rigid-body
+stream) states which tasks a simulation step emits given the island counts that
+the caller's own simulation produced. It holds no dependency detection, no
+scheduling and no task-body arithmetic: the CPU oracle (``oracle/``) and the
+CUDA path (``paper_2401_12377_b300``) each implement those on their own and both
+read the streams built here.
+
+A stream is a list of :class:`Task`. Array operands are :class:`Ref` triples
+``(buffer name, element offset, element count)`` into named numpy buffers; the
+consumer maps buffer names to its own storage (numpy arrays on the CPU, device
+allocations on the GPU) and derives byte segments from the refs with its own
+address-resolution code.
+
+Workload shapes follow the paper's two workload classes (small kernels of a few
+CTAs, Sec. II "Case Study 1/2"): the paper's own benchmarks (Brax physics
+environments, InstaNAS / dynamic-routing DNNs on CIFAR10 / Cityscapes) are not
+available, so these synthetic streams stand in for them by shape only.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, NamedTuple, Optional
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """One output of the SplitMix64 generator (Steele, Lea, Flood; OOPSLA 2014)
+    seeded with ``x``: a counter-based hash used for seeded per-task choices."""
+    z = (x + 0x9E3779B97F4A7C15) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def mix(*keys: int) -> int:
+    """Hash a tuple of small non-negative integers to 64 bits (chained SplitMix64)."""
+    h = 0x2545F4914F6CDD1D
+    for k in keys:
+        h = splitmix64(h ^ (k & MASK64))
+    return h
+
+
+class Ref(NamedTuple):
+    """A contiguous element range ``buf[off : off + n]`` of a named buffer."""
+    buf: str
+    off: int
+    n: int
+
+
+@dataclass
+class Task:
+    """One small kernel invocation in program order.
+
+    ``op`` names the body; ``arrays`` maps operand roles to :class:`Ref`;
+    ``scalars`` maps scalar roles to numpy scalars (float32 / uint32).
+    ``ncta`` is the CTA count the task is launched with.
+    """
+    task_id: int
+    op: str
+    ncta: int
+    arrays: Dict[str, Ref]
+    scalars: Dict[str, object] = field(default_factory=dict)
+
+
+@dataclass
+class Stream:
+    """A complete stream: initial buffers, tasks in program order, window size."""
+    buffers: Dict[str, np.ndarray]
+    tasks: List[Task]
+    window: int
+    name: str = ""
+
+
+# ----------------------------------------------------------------------------
+# Elementwise stream (16 buffers x 4096 floats, axpy / scale / add)
+# ----------------------------------------------------------------------------
+
+def elementwise_stream(seed: int, n_tasks: int = 64, n_buffers: int = 16,
+                       n_elems: int = 4096, window: int = 8,
+                       ranges: bool = False, max_ncta: int = 4) -> Stream:
+    """Tiny synthetic stream of axpy / scale / add tasks.
+
+    Each task picks its op uniformly, reads one (scale) or two (axpy, add)
+    buffers and writes one buffer, all chosen uniformly (a written buffer may
+    alias an input). ``a`` ~ U[0.5, 1.5), ``ncta`` ~ U{1..max_ncta}, buffer
+    contents ~ U[-1, 1). With ``ranges`` every task instead works on one
+    random sub-range ``[off, off + n)`` (same ``n`` for all its operands, any
+    element alignment), which produces partial segment overlaps.
+    """
+    rng = np.random.default_rng(seed)
+    bufs = {f"b{i}": rng.uniform(-1.0, 1.0, n_elems).astype(np.float32)
+            for i in range(n_buffers)}
+    tasks = []
+    for t in range(n_tasks):
+        op = ("axpy", "scale", "add")[int(rng.integers(0, 3))]
+        ncta = int(rng.integers(1, max_ncta + 1))
+        names = [f"b{int(i)}" for i in rng.integers(0, n_buffers, 3)]
+        if ranges:
+            # operands naming the same buffer share one offset: a task's own
+            # reads and writes alias exactly or not at all (elementwise-safe)
+            n = int(rng.integers(1, n_elems + 1))
+            by_buf = {}
+            offs = [by_buf.setdefault(nm, int(rng.integers(0, n_elems - n + 1))) for nm in names]
+        else:
+            n, offs = n_elems, [0, 0, 0]
+        refs = [Ref(names[i], offs[i], n) for i in range(3)]
+        a = np.float32(rng.uniform(0.5, 1.5))
+        if op == "axpy":
+            tasks.append(Task(t, op, ncta, {"x": refs[0], "y": refs[1]}, {"a": a}))
+        elif op == "scale":
+            tasks.append(Task(t, op, ncta, {"x": refs[0], "y": refs[1]}, {"a": a}))
+        else:
+            tasks.append(Task(t, op, ncta, {"x": refs[0], "y": refs[1], "z": refs[2]}))
+    return Stream(bufs, tasks, window, f"elementwise(seed={seed},ranges={ranges})")
+
+
+# ----------------------------------------------------------------------------
+# Dynamic-DNN stream (gated residual MLP, hidden 256, 24 blocks)
+# ----------------------------------------------------------------------------
+
+GEMV_NCTA_CHOICES = (1, 2, 4, 8, 16, 32)
+
+
+def dnn_gate(seed: int, sample: int, block: int) -> int:
+    """Per-sample block gate (keep probability 1/2): 1 runs the block."""
+    return int((mix(seed, 0xD5, sample, block) >> 17) & 1)
+
+
+def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
+               window: int = 32, task_id0: int = 0) -> Stream:
+    """Gated residual MLP inference for ``batch`` samples, in block-major order.
+
+    Block k of sample s runs iff ``dnn_gate(seed, s, k)``; a run block is four
+    tasks: ``t_s = W1_k h_s`` (GEMV), ``t_s = relu(t_s + b1_k)``,
+    ``u_s = W2_k t_s`` (GEMV), ``h_s = h_s + (u_s + b2_k)``. Weights and biases
+    ~ U[-1/16, 1/16), inputs ~ U[-1, 1). Activations are per sample, so the
+    samples' chains are independent; weights are shared read-only. GEMV tasks
+    use 1..32 CTAs (seeded), the elementwise ones 1 CTA.
+    """
+    rng = np.random.default_rng(seed)
+    H = hidden
+    W = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H, H)).astype(np.float32)
+    B = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H)).astype(np.float32)
+    h = rng.uniform(-1.0, 1.0, (batch, H)).astype(np.float32)
+    bufs = {"W": W.reshape(-1), "B": B.reshape(-1), "h": h.reshape(-1),
+            "t": np.zeros(batch * H, np.float32), "u": np.zeros(batch * H, np.float32)}
+    tasks = []
+    tid = task_id0
+    for k in range(blocks):
+        for s in range(batch):
+            if not dnn_gate(seed, s, k):
+                continue
+            w1 = Ref("W", (k * 2 + 0) * H * H, H * H)
+            w2 = Ref("W", (k * 2 + 1) * H * H, H * H)
+            b1 = Ref("B", (k * 2 + 0) * H, H)
+            b2 = Ref("B", (k * 2 + 1) * H, H)
+            hs, ts, us = Ref("h", s * H, H), Ref("t", s * H, H), Ref("u", s * H, H)
+            c1 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 1) % len(GEMV_NCTA_CHOICES)]
+            c2 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 2) % len(GEMV_NCTA_CHOICES)]
+            dims = {"m": np.uint32(H), "k": np.uint32(H)}
+            tasks.append(Task(tid, "gemv", c1, {"W": w1, "x": hs, "y": ts}, dict(dims))); tid += 1
+            tasks.append(Task(tid, "bias_relu", 1, {"t": ts, "b": b1})); tid += 1
+            tasks.append(Task(tid, "gemv", c2, {"W": w2, "x": ts, "y": us}, dict(dims))); tid += 1
+            tasks.append(Task(tid, "resid", 1, {"h": hs, "u": us, "b": b2})); tid += 1
+    return Stream(bufs, tasks, window, f"dnn(seed={seed},batch={batch})")
+
+
+# ----------------------------------------------------------------------------
+# Rigid-body RL-simulation stream (E envs x S spheres; input-dependent DAG)
+# ----------------------------------------------------------------------------
+
+RL_SPHERES = 32                 # spheres per environment (fixed by the record layout)
+RL_REC_BYTES = 1088             # bytes of one environment's contact record
+RL_PAIRS = RL_SPHERES * (RL_SPHERES - 1) // 2
+
+
+@dataclass
+class RLParams:
+    n_env: int = 256
+    steps: int = 50
+    chunk: int = 8              # environments per broadphase / integrate task
+    box: float = 0.9            # cubic box edge L (about 300 tasks per step)
+    dt: float = 1.0 / 240.0
+    gravity: float = -9.81
+    beta: float = 0.2           # Baumgarte position-error feedback
+    slop: float = 0.001
+    max_solve_ncta: int = 16
+    max_chunk_ncta: int = 4
+
+
+class RLSim:
+    """Task emission for the rigid-sphere stream.
+
+    Per step t the program order is: one ``rl_solve`` task for every
+    environment whose contact record reports at least one island, in
+    environment order (``ncta = clamp(islands, 1, 16)``); then one
+    ``rl_integrate`` task per chunk of environments; then (except after the
+    last step) one ``rl_broadphase`` task per chunk for step t+1. The stream
+    starts with the broadphase tasks of step 0. Because the solve tasks exist
+    only where contacts were found, the DAG depends on the simulated state.
+
+    The caller runs each emitted batch with its own implementation, reads the
+    per-environment island counts (buffer ``nisl``) that its broadphase wrote,
+    and passes them to :meth:`step_batch`.
+    """
+
+    def __init__(self, seed: int, params: Optional[RLParams] = None):
+        self.seed = seed
+        self.p = params or RLParams()
+        if self.p.n_env % self.p.chunk:
+            raise ValueError("n_env must be a multiple of chunk")
+        self.next_id = 0
+
+    # -- initial state -------------------------------------------------------
+    def buffers(self) -> Dict[str, np.ndarray]:
+        p, S = self.p, RL_SPHERES
+        rng = np.random.default_rng(self.seed)
+        radius = rng.uniform(0.05, 0.1, (p.n_env, S)).astype(np.float32)
+        invmass = rng.uniform(0.5, 2.0, (p.n_env, S)).astype(np.float32)
+        u = rng.uniform(0.0, 1.0, (p.n_env, S, 3))
+        lo = radius[..., None].astype(np.float64)
+        pos = (lo + u * (p.box - 2.0 * lo)).astype(np.float32)
+        vel = rng.uniform(-0.5, 0.5, (p.n_env, S, 3)).astype(np.float32)
+        prop = np.stack([radius, invmass], axis=-1).astype(np.float32)
+        return {"pos": pos.reshape(-1), "vel": vel.reshape(-1), "prop": prop.reshape(-1),
+                "cont": np.zeros(p.n_env * RL_REC_BYTES, np.uint8),
+                "nisl": np.zeros(p.n_env, np.uint32)}
+
+    @property
+    def window(self) -> int:
+        return 32
+
+    # -- helpers -----------------------------------------------------------------
+    def _chunk_ncta(self, kind: int, step: int, c: int) -> int:
+        return 1 + mix(self.seed, 0x71, kind, step, c) % self.p.max_chunk_ncta
+
+    def _refs_env(self, e0: int, ne: int):
+        S = RL_SPHERES
+        return (Ref("pos", e0 * S * 3, ne * S * 3), Ref("vel", e0 * S * 3, ne * S * 3),
+                Ref("prop", e0 * S * 2, ne * S * 2), Ref("cont", e0 * RL_REC_BYTES, ne * RL_REC_BYTES),
+                Ref("nisl", e0, ne))
+
+    def _emit(self, op, ncta, arrays, scalars=None) -> Task:
+        t = Task(self.next_id, op, int(ncta), arrays, scalars or {})
+        self.next_id += 1
+        return t
+
+    def _broadphase(self, step: int) -> List[Task]:
+        p, out = self.p, []
+        for c in range(p.n_env // p.chunk):
+            pos, _, prop, cont, nisl = self._refs_env(c * p.chunk, p.chunk)
+            out.append(self._emit("rl_broadphase", self._chunk_ncta(0, step, c),
+                                  {"pos": pos, "prop": prop, "cont": cont, "nisl": nisl},
+                                  {"nenv": np.uint32(p.chunk)}))
+        return out
+
+    # -- batches -------------------------------------------------------------------
+    def first_batch(self) -> List[Task]:
+        """Broadphase of step 0."""
+        return self._broadphase(0)
+
+    def step_batch(self, step: int, nisl: np.ndarray) -> List[Task]:
+        """Solve + integrate of ``step`` and broadphase of ``step + 1``."""
+        p = self.p
+        nisl = np.asarray(nisl).reshape(-1)
+        if nisl.shape[0] != p.n_env:
+            raise ValueError("nisl must hold one count per environment")
+        out = []
+        f32 = np.float32
+        beta_dt = f32(f32(p.beta) / f32(p.dt))
+        for e in range(p.n_env):
+            k = int(nisl[e])
+            if k <= 0:
+                continue
+            pos, vel, prop, cont, _ = self._refs_env(e, 1)
+            out.append(self._emit("rl_solve", min(max(k, 1), p.max_solve_ncta),
+                                  {"pos": pos, "vel": vel, "prop": prop, "cont": cont},
+                                  {"beta_dt": beta_dt, "slop": f32(p.slop)}))
+        dt = f32(p.dt)
+        gdt = f32(f32(p.gravity) * dt)
+        for c in range(p.n_env // p.chunk):
+            pos, vel, prop, _, _ = self._refs_env(c * p.chunk, p.chunk)
+            out.append(self._emit("rl_integrate", self._chunk_ncta(1, step, c),
+                                  {"pos": pos, "vel": vel, "prop": prop},
+                                  {"nenv": np.uint32(p.chunk), "dt": dt, "gdt": gdt,
+                                   "box": f32(p.box)}))
+        if step + 1 < p.steps:
+            out.extend(self._broadphase(step + 1))
+        return out
+
+
+# ----------------------------------------------------------------------------
+# Sleep stream (scheduler micro-benchmarks: known body time, chosen DAG shape)
+# ----------------------------------------------------------------------------
+
+def sleep_chain_stream(n_tasks: int, sleep_ns: int, width: int, window: int = 32,
+                       ncta: int = 1) -> Stream:
+    """``width`` independent chains interleaved round-robin; each task sleeps
+    ``sleep_ns`` and then sets ``y[0] = y[0] * 0.5 + tag`` on its chain's
+    buffer (so tasks of one chain conflict and chains are independent)."""
+    bufs = {f"c{i}": np.zeros(16, np.float32) for i in range(width)}
+    tasks = [Task(t, "sleep", ncta, {"y": Ref(f"c{t % width}", 0, 1)},
+                  {"ns": np.uint32(sleep_ns), "tag": np.float32(t % 7 + 1)})
+             for t in range(n_tasks)]
+    return Stream(bufs, tasks, window, f"sleep(n={n_tasks},w={width})")
+
+
+# ----------------------------------------------------------------------------
+# Batched streams (many independent streams of uneven length)
+# ----------------------------------------------------------------------------
+
+def loguniform_lengths(seed: int, n: int, lo: int = 100, hi: int = 5000) -> List[int]:
+    rng = np.random.default_rng(seed)
+    return [int(round(math.exp(x))) for x in rng.uniform(math.log(lo), math.log(hi), n)]
