@@ -1,0 +1,276 @@
+/*
+ * acs.h -- C ABI of the B300 out-of-order task scheduler (libacs.so).
+ *
+ * Implements the runtime problem of ACS (arXiv 2401.12377): small GPU tasks are
+ * submitted in program order together with the byte ranges each reads and
+ * writes; dependencies between them are found at run time by testing those
+ * ranges for overlap within a sliding scheduling window (Sec. III-C, Alg. 1),
+ * and every task is issued as soon as its upstream tasks have retired
+ * (ready / pending / executing states, Sec. III-C and Sec. IV-C).
+ *
+ * Here the window, the dependency test, the state machine and the dispatch all
+ * live in one persistent, cooperatively launched CUDA kernel (sm_103a): one
+ * scheduler warp per stream keeps the stream's window in shared memory and
+ * hands ready tasks' CTAs to resident worker CTAs through a device work ring,
+ * so no task costs a host round trip.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ACS_OK (0) or a negative ACS_ERR_* code.
+ *   - Errors are sticky: after the first error a context returns it from every
+ *     later call except acs_get_stats / acs_get_log / acs_destroy.
+ *   - A context belongs to one host thread; calls on one context must not race.
+ *   - Pointers inside acs_args are DEVICE addresses of caller-owned memory,
+ *     which must stay allocated until acs_sync has returned for the tasks using
+ *     it. All other pointer arguments are HOST memory, read or written only
+ *     during the call.
+ */
+#ifndef ACS_H
+#define ACS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define ACS_OK              0
+#define ACS_ERR_INVALID    (-1)  /* bad argument: window, stream, op, ncta, segment */
+#define ACS_ERR_FULL       (-2)  /* stream ring full: acs_flush + acs_sync, then retry */
+#define ACS_ERR_TIMEOUT    (-3)  /* a bounded device wait expired (no progress) */
+#define ACS_ERR_DEVICE     (-4)  /* a CUDA runtime call failed */
+#define ACS_ERR_STOPPED    (-5)  /* the context was stopped */
+#define ACS_ERR_ORDER      (-6)  /* task_id not strictly increasing within a stream */
+#define ACS_ERR_NOMEM      (-7)  /* host or device allocation failed */
+
+/* ---- limits ------------------------------------------------------------- */
+#define ACS_MAX_WINDOW     64    /* W: slots of the scheduling window per stream */
+#define ACS_MAX_SEGS       16    /* read + write segments per task (non-empty ones) */
+#define ACS_MAX_NCTA       256   /* CTAs per task */
+#define ACS_MAX_STREAMS    256   /* independent streams per context */
+#define ACS_BLOCK_THREADS  256   /* threads of every task CTA */
+
+/*
+ * A byte range [start, start + size) of device memory that a task reads or
+ * writes (the paper's read_segments / write_segments entries, Sec. III-C and
+ * Sec. IV-A). size == 0 is dropped (it never conflicts). {0, UINT64_MAX} is
+ * "all of memory", the paper's rule for kernels with indirect accesses whose
+ * ranges are unknown (Sec. IV-A). Any other range whose end overflows 2^64 is
+ * rejected with ACS_ERR_INVALID.
+ */
+typedef struct acs_segment {
+    uint64_t start;
+    uint64_t size;
+} acs_segment;
+
+#define ACS_WHOLE_MEMORY_START 0ull
+#define ACS_WHOLE_MEMORY_SIZE  UINT64_MAX
+
+/* ---- task bodies ---------------------------------------------------------
+ * Every task runs one of these bodies on ncta CTAs of ACS_BLOCK_THREADS
+ * threads. Arithmetic is fp32 with round-to-nearest and no contraction of
+ * multiply-add except where stated, so a task's output does not depend on ncta
+ * or on the schedule. */
+enum acs_op {
+    ACS_OP_NOP = 0,           /* no body; segments as given                     */
+    ACS_OP_AXPY = 1,          /* y[i] = a*x[i] + y[i]              acs_axpy_args */
+    ACS_OP_SCALE = 2,         /* y[i] = a*x[i]                     acs_axpy_args */
+    ACS_OP_ADD = 3,           /* z[i] = x[i] + y[i]                acs_add_args  */
+    ACS_OP_GEMV = 4,          /* y = W x, W row-major m x k, fp32 fused-multiply-add
+                                 accumulation in a fixed order    acs_gemv_args */
+    ACS_OP_BIAS_RELU = 5,     /* t[i] = max(t[i] + b[i], +0)       acs_bias_relu_args */
+    ACS_OP_RESID = 6,         /* h[i] = h[i] + (u[i] + b[i])       acs_resid_args */
+    ACS_OP_RL_BROADPHASE = 10,/* sphere contacts + islands per env acs_rl_broadphase_args */
+    ACS_OP_RL_SOLVE = 11,     /* Gauss-Seidel contact impulses, 1 env acs_rl_solve_args */
+    ACS_OP_RL_INTEGRATE = 12, /* semi-implicit Euler + box walls   acs_rl_integrate_args */
+    ACS_OP_WAIT_FLAG = 30,    /* test body: wait until *flag != 0, the stop flag, or
+                                 limit_ns elapsed                  acs_wait_args */
+    ACS_OP_SLEEP = 31         /* spin ns, then y[0] = y[0]*0.5 + tag (CTA 0)
+                                                                   acs_sleep_args */
+};
+
+/* Packed launch arguments of one task: op, CTA count and up to 48 bytes of
+ * op-specific arguments (one of the acs_*_args structs below, memcpy'd into
+ * bytes). Copied by acs_submit*. */
+typedef struct acs_args {
+    uint16_t op;        /* enum acs_op */
+    uint16_t ncta;      /* 1 .. ACS_MAX_NCTA */
+    uint32_t reserved;  /* must be 0 */
+    uint8_t bytes[48];
+} acs_args;
+
+typedef struct { uint64_t x, y; uint32_t n; float a; } acs_axpy_args;
+typedef struct { uint64_t x, y, z; uint32_t n; uint32_t pad; } acs_add_args;
+typedef struct { uint64_t W, x, y; uint32_t m, k; } acs_gemv_args;
+typedef struct { uint64_t t, b; uint32_t n; uint32_t pad; } acs_bias_relu_args;
+typedef struct { uint64_t h, u, b; uint32_t n; uint32_t pad; } acs_resid_args;
+
+/* Rigid-sphere workload: 32 spheres per environment.
+ *   pos  fp32 [env][32][3]    vel fp32 [env][32][3]    prop fp32 [env][32][2] (radius, 1/mass)
+ *   cont contact record per env, ACS_RL_REC_BYTES bytes:
+ *        u32 ncontact, u32 nisland, u8 label[32] (smallest sphere index of its
+ *        component), u8 root[32] (labels of islands with >= 1 contact, ascending),
+ *        u16 pair[496] (i | j << 8, i < j, lexicographic), zero padding.
+ *   nisl u32 [env] island count (copy of the record's nisland). */
+#define ACS_RL_SPHERES   32
+#define ACS_RL_REC_BYTES 1088
+typedef struct { uint64_t pos, prop, cont, nisl; uint32_t nenv; uint32_t pad; } acs_rl_broadphase_args;
+typedef struct { uint64_t pos, prop, cont, vel; float beta_dt, slop; } acs_rl_solve_args;
+typedef struct { uint64_t pos, vel, prop; uint32_t nenv; float dt, gdt, box; } acs_rl_integrate_args;
+typedef struct { uint64_t flag; uint64_t limit_ns; } acs_wait_args;
+typedef struct { uint64_t y; uint64_t ns; float tag; uint32_t pad; } acs_sleep_args;
+
+/* ---- context configuration ----------------------------------------------- */
+enum acs_mode {
+    ACS_MODE_WINDOW = 0,   /* the method: persistent device scheduler (default) */
+    ACS_MODE_INORDER = 1,  /* baseline: one kernel launch per task, one CUDA stream */
+    ACS_MODE_GRAPH = 2     /* baseline: per flush, a CUDA graph of the full DAG */
+};
+
+enum acs_flags {
+    ACS_FLAG_LOG = 1,      /* record per-task upstream-candidate masks and
+                              start / retire tickets (window mode) */
+    ACS_FLAG_TIMING = 2    /* time each device launch with CUDA events */
+};
+
+typedef struct acs_config {
+    uint32_t mode;          /* enum acs_mode */
+    uint32_t n_streams;     /* independent task streams, 1 .. ACS_MAX_STREAMS (0 -> 1) */
+    uint32_t cta_slots;     /* worker CTAs of the persistent kernel (0 -> every
+                               co-resident CTA not used by a scheduler) */
+    uint32_t capacity;      /* ring entries per stream, rounded up to a power of
+                               two >= 64 (0 -> 8192); bounds tasks in flight */
+    uint32_t log_capacity;  /* log entries per stream (0 -> capacity) */
+    uint32_t flags;         /* enum acs_flags */
+    uint64_t timeout_ns;    /* bound on every device wait without progress (0 -> 5 s) */
+    void *cuda_stream;      /* cudaStream_t for all device work (NULL -> a
+                               non-blocking stream owned by the context) */
+    int32_t device;         /* CUDA device ordinal (-1 -> current) */
+    uint32_t reserved[7];   /* must be 0 */
+} acs_config;
+
+typedef struct acs_stats {
+    uint64_t tasks_submitted;
+    uint64_t tasks_flushed;
+    uint64_t launches;          /* persistent launches (window) / kernels (in-order) / graphs */
+    uint64_t seg_bytes;         /* sum of read + write segment sizes of flushed tasks,
+                                   whole-memory segments excluded */
+    double kernel_ms;           /* ACS_FLAG_TIMING: device time of the launches, summed */
+    double graph_build_ms;      /* graph mode: host time to build graphs (incl. DAG) */
+    double graph_instantiate_ms;/* graph mode: host time in cudaGraphInstantiate */
+    uint64_t graph_edges;       /* graph mode: edges after transitive reduction */
+    uint64_t sched_cycles;      /* window mode: SM clock cycles the scheduler warps ran */
+    uint64_t sched_busy_cycles; /* ... of which spent inserting, retiring, dispatching */
+    uint64_t sched_inserts;     /* tasks inserted into windows */
+    uint32_t cta_slots;         /* worker CTAs of the persistent kernel */
+    uint32_t grid;              /* total CTAs of the persistent kernel */
+} acs_stats;
+
+typedef struct acs_ctx acs_ctx;
+
+/* Fill *cfg with the defaults (all zero fields mean "default"). */
+void acs_config_default(acs_config *cfg);
+
+/*
+ * Create a context with a scheduling window of `window` slots per stream
+ * (Sec. III-C: a fixed-size window of N kernels filled in FIFO order; the paper
+ * evaluates N = 16 and 32, Sec. VI-D). 1 <= window <= ACS_MAX_WINDOW. cfg may
+ * be NULL. Allocates the context's device rings and pinned host rings; frees
+ * them in acs_destroy. *out is set only on success.
+ * Errors: ACS_ERR_INVALID (window, n_streams, mode, reserved fields),
+ * ACS_ERR_DEVICE, ACS_ERR_NOMEM.
+ */
+int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg);
+
+/*
+ * Resolve the read and write segments of a task from its packed arguments:
+ * the get_addresses wrapper of Sec. IV-A (Fig. get_addresses: a matrix product
+ * reads its two inputs, m*n and n*k elements, and writes its m*k output). The
+ * result is what acs_submit_ops submits. reads / writes must hold
+ * ACS_MAX_SEGS entries; *n_reads / *n_writes receive the counts.
+ * Errors: ACS_ERR_INVALID (unknown op, sizes overflowing 64 bits).
+ */
+int acs_get_addresses(const acs_args *args, acs_segment *reads, uint32_t *n_reads,
+                      acs_segment *writes, uint32_t *n_writes);
+
+/*
+ * Append one task to stream 0 in program order (Sec. III-D: invoked kernels
+ * and their segments enter the input FIFO). Copies args and both segment
+ * arrays. task_id must be strictly greater than the previous task_id of the
+ * stream (it names the task in logs). At most ACS_MAX_SEGS non-empty segments.
+ * Nothing runs until acs_flush.
+ * Errors: ACS_ERR_INVALID, ACS_ERR_ORDER, ACS_ERR_FULL (more than
+ * capacity - window + 1 tasks since the last acs_sync).
+ */
+int acs_submit(acs_ctx *ctx, uint32_t task_id, const acs_args *args,
+               const acs_segment *reads, uint32_t n_reads,
+               const acs_segment *writes, uint32_t n_writes);
+
+/* acs_submit on stream `stream` (0 <= stream < n_streams). Streams are
+ * independent programs: no dependency is ever detected across streams. */
+int acs_submit_stream(acs_ctx *ctx, uint32_t stream, uint32_t task_id, const acs_args *args,
+                      const acs_segment *reads, uint32_t n_reads,
+                      const acs_segment *writes, uint32_t n_writes);
+
+/* Submit n tasks to `stream`, each with the segments acs_get_addresses
+ * derives from its args. task_ids and args are arrays of n entries. Stops at
+ * the first failing task and returns its error (earlier tasks stay submitted). */
+int acs_submit_ops(acs_ctx *ctx, uint32_t stream, uint32_t n, const uint32_t *task_ids,
+                   const acs_args *args);
+
+/*
+ * Make every task submitted since the last flush runnable and start running it,
+ * without blocking the host. Window mode: copies the new descriptors into the
+ * device rings and launches the persistent scheduler kernel (cooperative
+ * launch) over them; windows continue across flushes, so dependency detection
+ * is identical however a stream is split into flushes. In-order mode: launches
+ * one kernel per task. Graph mode: builds, instantiates and launches a CUDA
+ * graph of the flushed tasks' full DAG.
+ * Errors: ACS_ERR_DEVICE (launch failed, e.g. the grid cannot be co-resident).
+ */
+int acs_flush(acs_ctx *ctx);
+
+/*
+ * Block until every flushed task retired (all CTAs finished, their global
+ * writes visible). Returns the context's first error, e.g. ACS_ERR_TIMEOUT if
+ * a device wait made no progress for timeout_ns.
+ */
+int acs_sync(acs_ctx *ctx);
+
+/*
+ * Copy the window-mode log of tasks [first, first + n) of `stream` (positions in
+ * submission order) into host arrays of n entries each (any may be NULL):
+ *   masks[i]  upstream candidates of the task at insertion: bit b set iff the
+ *             task in window slot b (the unique earlier task t with
+ *             t mod window == b among the window - 1 previous tasks)
+ *             conflicts with it, whether or not that task had already retired;
+ *   start[i]  smallest ticket drawn by the task's CTAs when they began;
+ *   retire[i] ticket drawn when its last CTA finished.
+ * Tickets come from one device counter. Needs ACS_FLAG_LOG and a completed
+ * acs_sync; the range must lie within the last log_capacity tasks.
+ * Errors: ACS_ERR_INVALID.
+ */
+int acs_get_log(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n,
+                uint64_t *masks, uint64_t *start, uint64_t *retire);
+
+/* Copy the context's counters into *out (after acs_sync for device figures). */
+int acs_get_stats(acs_ctx *ctx, acs_stats *out);
+
+/* Graph mode: launch the most recently instantiated graph again (timing of a
+ * prebuilt graph; re-runs its tasks). Errors: ACS_ERR_INVALID if none. */
+int acs_graph_replay(acs_ctx *ctx);
+
+/* The context's sticky error (ACS_OK if none). */
+int acs_error(const acs_ctx *ctx);
+
+/* Static description of a status code. */
+const char *acs_strerror(int code);
+
+/* Synchronize, then free everything the context allocated. NULL is a no-op. */
+void acs_destroy(acs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACS_H */

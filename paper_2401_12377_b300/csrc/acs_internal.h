@@ -1,0 +1,127 @@
+// Internal layouts shared by the host runtime (acs_runtime.cu) and the device
+// code (acs_kernels.cu). Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+
+#include "acs.h"
+
+namespace acs {
+
+constexpr int kBlock = ACS_BLOCK_THREADS;
+constexpr int kMaxSegs = ACS_MAX_SEGS;
+constexpr int kMaxWindow = ACS_MAX_WINDOW;
+constexpr int kPrefetch = 16;          // descriptors per prefetch batch (bulk copy)
+constexpr int kRowSegs = kMaxSegs + 1; // window row stride in segments (1 pad: bank spread)
+constexpr int kBodySmem = 4096;        // shared memory reserved for task bodies
+constexpr uint32_t kMinCapacity = 64;
+
+// An inclusive byte range [start, last]; empty segments are never stored.
+struct Seg {
+    uint64_t start;
+    uint64_t last;
+};
+
+// One task descriptor, 320 bytes, at ring position (seq mod capacity) of its
+// stream. The first 64 bytes are what a worker CTA needs; the segments are
+// what the scheduler needs.
+struct alignas(16) TaskRec {
+    uint32_t task_id;
+    uint16_t op;
+    uint16_t ncta;
+    uint16_t wmask;      // bit k set: seg[k] is a write segment
+    uint8_t nseg;
+    uint8_t flags;
+    uint32_t seq;        // position of the task in its stream
+    uint8_t args[48];
+    Seg seg[kMaxSegs];
+};
+static_assert(sizeof(TaskRec) == 320, "TaskRec layout");
+
+struct alignas(16) TaskHdr {   // the first 64 bytes of a TaskRec
+    uint32_t task_id;
+    uint16_t op;
+    uint16_t ncta;
+    uint16_t wmask;
+    uint8_t nseg;
+    uint8_t flags;
+    uint32_t seq;
+    uint8_t args[48];
+};
+static_assert(sizeof(TaskHdr) == 64, "TaskHdr layout");
+
+// Device-resident counters of one context; hot words on separate 128 B lines.
+struct alignas(128) DevCtl {
+    uint32_t ring_head;     // work-ring positions claimed by worker CTAs
+    uint32_t pad0[31];
+    uint32_t ring_tail;     // work-ring positions reserved by scheduler warps
+    uint32_t pad1[31];
+    uint32_t stop;          // 1: every CTA leaves its loop
+    uint32_t sched_done;    // scheduler warps that finished their streams
+    uint32_t exit_count;    // CTAs that left the kernel
+    uint32_t err;           // first error (ACS_ERR_*), 0 = none
+    uint32_t err_info;      // where: 1 scheduler, 2 worker, 3 producer ring, 4 prefetch
+    uint32_t pad2[27];
+    unsigned long long ticket;  // legality-log ticket counter
+    uint32_t pad3[30];
+};
+
+// Written by the last CTA of each persistent launch into mapped host memory.
+struct HostStatus {
+    volatile uint32_t err;
+    volatile uint32_t err_info;
+    volatile uint32_t launches_done;
+    volatile uint32_t pad;
+};
+
+// Per-stream scheduler statistics (device), accumulated over launches.
+struct SchedStats {
+    unsigned long long cycles;
+    unsigned long long busy_cycles;
+    unsigned long long inserts;
+    unsigned long long pad;
+};
+
+struct KParams {
+    TaskRec *recs;            // [n_streams][capacity]
+    DevCtl *ctl;
+    unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
+    uint32_t *done;           // [n_streams][kMaxWindow]: seq + 1 of the slot's retired task
+    uint32_t *remaining;      // [n_streams][kMaxWindow]: CTAs of the slot's task that finished
+    unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
+    SchedStats *sched_stats;  // [n_streams]
+    HostStatus *hstatus;      // mapped host memory
+    unsigned long long timeout_ns;
+    uint32_t cap_log2;        // capacity = 1 << cap_log2
+    uint32_t log_log2;        // log_capacity = 1 << log_log2
+    uint32_t cell_mask;       // work-ring cells - 1 (power of two)
+    uint32_t window;
+    uint32_t n_streams;       // = scheduler CTAs (CTA s < n_streams schedules stream s)
+    uint32_t flags;
+    uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses
+    uint32_t pad;
+    uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
+    uint32_t end[ACS_MAX_STREAMS];    // one past the last seq of this launch
+};
+
+inline uint32_t sched_smem_bytes(uint32_t window) {
+    uint32_t rows = window * kRowSegs * (uint32_t)sizeof(Seg);
+    uint32_t meta = window * 4;                       // wmask (u16) + nseg (u8) + pad
+    uint32_t pf = 2 * kPrefetch * (uint32_t)sizeof(TaskRec);
+    uint32_t total = rows + meta;
+    total = (total + 127) & ~127u;
+    return total + pf + 64;                           // + two mbarriers
+}
+
+inline uint32_t dyn_smem_bytes(uint32_t window) {
+    uint32_t s = sched_smem_bytes(window);
+    return s > (uint32_t)kBodySmem ? s : (uint32_t)kBodySmem;
+}
+
+// Task states of a window slot (scheduler registers).
+enum SlotState : uint32_t { kEmpty = 0, kPending = 1, kReady = 2, kExec = 3, kRetired = 4 };
+
+// error-site codes stored in DevCtl::err_info
+enum ErrSite : uint32_t { kSiteSched = 1, kSiteWorker = 2, kSiteRing = 3, kSitePrefetch = 4 };
+
+}  // namespace acs

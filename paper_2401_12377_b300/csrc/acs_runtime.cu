@@ -1,0 +1,720 @@
+// Host side of libacs: the C ABI declared in include/acs.h.
+//
+// acs_submit* validates a task and writes its 320-byte descriptor straight
+// into a pinned host ring that mirrors the stream's device ring position for
+// position. acs_flush copies the new range with one cudaMemcpyAsync per stream
+// (two where the ring wraps) and, in window mode, starts the persistent
+// scheduler kernel with a cooperative launch (which fails instead of
+// oversubscribing, so every scheduler and worker CTA is co-resident). That
+// copy is the only host->device crossing per flush; nothing crosses per task.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "acs_internal.h"
+
+namespace acs {
+const void *persistent_kernel_fn();
+const void *body_kernel_fn();
+cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, uint32_t *done, uint32_t *remaining,
+                        uint32_t nslots, cudaStream_t st);
+}  // namespace acs
+
+using namespace acs;
+
+namespace {
+
+struct StreamState {
+    uint32_t submitted = 0;  // next seq
+    uint32_t flushed = 0;    // seqs below were handed to the device
+    uint32_t synced = 0;     // seqs below are known retired (last acs_sync)
+    bool has_id = false;
+    uint32_t last_id = 0;
+};
+
+struct TimedLaunch {
+    cudaEvent_t a, b;
+};
+
+uint32_t log2_pow2(uint32_t v) {
+    uint32_t l = 0;
+    while ((1u << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct acs_ctx {
+    acs_config cfg{};
+    uint32_t W = 0, S = 0, C = 0, cap_log2 = 0, LC = 0, log_log2 = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    TaskRec *h_ring = nullptr;  // pinned [S][C]
+    TaskRec *d_ring = nullptr;
+    DevCtl *d_ctl = nullptr;
+    uint32_t *d_done = nullptr, *d_remaining = nullptr;
+    unsigned long long *d_cells = nullptr;
+    uint32_t ncells = 0;
+    unsigned long long *d_log_mask = nullptr, *d_log_start = nullptr, *d_log_retire = nullptr;
+    SchedStats *d_sched_stats = nullptr;
+    HostStatus *h_status = nullptr, *d_status = nullptr;
+    std::vector<StreamState> st;
+    int err = ACS_OK;
+    uint32_t grid = 0, cta_slots = 0, smem = 0;
+    acs_stats stats{};
+    std::vector<TimedLaunch> timed;     // launches whose events are not yet read
+    std::vector<TimedLaunch> event_pool;
+    // graph mode
+    cudaGraphExec_t last_exec = nullptr;
+    std::vector<cudaGraphExec_t> execs_pending;
+    std::vector<cudaGraph_t> graphs_pending;
+};
+
+namespace {
+
+int fail(acs_ctx *c, int code) {
+    if (c && c->err == ACS_OK) c->err = code;
+    return code;
+}
+
+int cuda_fail(acs_ctx *c, cudaError_t e) {
+    if (e == cudaSuccess) return ACS_OK;
+    if (e == cudaErrorMemoryAllocation) return fail(c, ACS_ERR_NOMEM);
+    return fail(c, ACS_ERR_DEVICE);
+}
+
+TimedLaunch get_events(acs_ctx *c) {
+    if (!c->event_pool.empty()) {
+        TimedLaunch t = c->event_pool.back();
+        c->event_pool.pop_back();
+        return t;
+    }
+    TimedLaunch t{};
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+    return t;
+}
+
+// Segment validation and conversion to the inclusive form; returns false on
+// overflow. Empty segments are skipped.
+bool add_segs(const acs_segment *s, uint32_t n, bool write, Seg *out, uint32_t &cnt, uint16_t &wmask,
+              uint64_t &bytes) {
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t a = s[i].start, z = s[i].size;
+        if (z == 0) continue;
+        Seg g;
+        if (a == ACS_WHOLE_MEMORY_START && z == ACS_WHOLE_MEMORY_SIZE) {
+            g.start = 0;
+            g.last = UINT64_MAX;
+        } else {
+            if (a != 0 && z - 1 > UINT64_MAX - a) return false;  // end past 2^64
+            g.start = a;
+            g.last = a + (z - 1);
+            bytes += z;
+        }
+        if (cnt >= (uint32_t)kMaxSegs) return false;
+        if (write) wmask |= (uint16_t)(1u << cnt);
+        out[cnt++] = g;
+    }
+    return true;
+}
+
+bool valid_op(uint16_t op) {
+    switch (op) {
+    case ACS_OP_NOP: case ACS_OP_AXPY: case ACS_OP_SCALE: case ACS_OP_ADD: case ACS_OP_GEMV:
+    case ACS_OP_BIAS_RELU: case ACS_OP_RESID: case ACS_OP_RL_BROADPHASE: case ACS_OP_RL_SOLVE:
+    case ACS_OP_RL_INTEGRATE: case ACS_OP_WAIT_FLAG: case ACS_OP_SLEEP:
+        return true;
+    default:
+        return false;
+    }
+}
+
+// conflict test of the host-side DAG builder (graph baseline): same rule as
+// the device window test, over inclusive ranges.
+bool recs_conflict(const TaskRec &i, const TaskRec &j) {
+    for (int x = 0; x < j.nseg; ++x) {
+        const bool xw = (j.wmask >> x) & 1u;
+        for (int y = 0; y < i.nseg; ++y) {
+            const bool yw = (i.wmask >> y) & 1u;
+            if ((xw || yw) && j.seg[x].start <= i.seg[y].last && i.seg[y].start <= j.seg[x].last) return true;
+        }
+    }
+    return false;
+}
+
+void collect_timing(acs_ctx *c) {
+    for (auto &t : c->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) c->stats.kernel_ms += ms;
+        c->event_pool.push_back(t);
+    }
+    c->timed.clear();
+}
+
+int copy_new_descriptors(acs_ctx *c) {
+    for (uint32_t s = 0; s < c->S; ++s) {
+        StreamState &ss = c->st[s];
+        uint32_t a = ss.flushed, b = ss.submitted;
+        while (a < b) {
+            const uint32_t pa = a & (c->C - 1);
+            const uint32_t n = std::min(b - a, c->C - pa);
+            const size_t off = (size_t)s * c->C + pa;
+            cudaError_t e = cudaMemcpyAsync(c->d_ring + off, c->h_ring + off, (size_t)n * sizeof(TaskRec),
+                                            cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            a += n;
+        }
+    }
+    return ACS_OK;
+}
+
+int flush_window(acs_ctx *c) {
+    int rc = copy_new_descriptors(c);
+    if (rc) return rc;
+    KParams P;
+    std::memset(&P, 0, sizeof P);
+    P.recs = c->d_ring;
+    P.ctl = c->d_ctl;
+    P.cells = c->d_cells;
+    P.done = c->d_done;
+    P.remaining = c->d_remaining;
+    P.log_mask = c->d_log_mask;
+    P.log_start = c->d_log_start;
+    P.log_retire = c->d_log_retire;
+    P.sched_stats = c->d_sched_stats;
+    P.hstatus = c->d_status;
+    P.timeout_ns = c->cfg.timeout_ns;
+    P.cap_log2 = c->cap_log2;
+    P.log_log2 = c->log_log2;
+    P.cell_mask = c->ncells - 1;
+    P.window = c->W;
+    P.n_streams = c->S;
+    P.flags = c->cfg.flags;
+    P.sched_smem = sched_smem_bytes(c->W);
+    for (uint32_t s = 0; s < c->S; ++s) {
+        P.first[s] = c->st[s].flushed;
+        P.end[s] = c->st[s].submitted;
+    }
+    void *args[] = {&P};
+    TimedLaunch t{};
+    const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
+    if (timing) {
+        t = get_events(c);
+        cudaEventRecord(t.a, c->stream);
+    }
+    cudaError_t e = cudaLaunchCooperativeKernel(persistent_kernel_fn(), dim3(c->grid), dim3(kBlock), args,
+                                                c->smem, c->stream);
+    if (e != cudaSuccess) {
+        if (timing) c->event_pool.push_back(t);
+        return cuda_fail(c, e);
+    }
+    if (timing) {
+        cudaEventRecord(t.b, c->stream);
+        c->timed.push_back(t);
+    }
+    c->stats.launches++;
+    return ACS_OK;
+}
+
+int flush_inorder(acs_ctx *c) {
+    const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
+    TimedLaunch t{};
+    if (timing) {
+        t = get_events(c);
+        cudaEventRecord(t.a, c->stream);
+    }
+    for (uint32_t s = 0; s < c->S; ++s) {
+        StreamState &ss = c->st[s];
+        for (uint32_t q = ss.flushed; q < ss.submitted; ++q) {
+            const TaskRec &r = c->h_ring[(size_t)s * c->C + (q & (c->C - 1))];
+            TaskHdr h;
+            std::memcpy(&h, &r, sizeof h);
+            void *args[] = {&h};
+            cudaError_t e = cudaLaunchKernel(body_kernel_fn(), dim3(r.ncta), dim3(kBlock), args, kBodySmem, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            c->stats.launches++;
+        }
+    }
+    if (timing) {
+        cudaEventRecord(t.b, c->stream);
+        c->timed.push_back(t);
+    }
+    return ACS_OK;
+}
+
+int flush_graph(acs_ctx *c) {
+    using clk = std::chrono::steady_clock;
+    auto t0 = clk::now();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(body_kernel_fn());
+    kp.blockDim = dim3(kBlock);
+    kp.sharedMemBytes = kBodySmem;
+    for (uint32_t s = 0; s < c->S; ++s) {
+        StreamState &ss = c->st[s];
+        const uint32_t n = ss.submitted - ss.flushed;
+        if (!n) continue;
+        std::vector<cudaGraphNode_t> nodes(n);
+        const uint32_t words = (n + 63) / 64;
+        std::vector<uint64_t> reach((size_t)n * words, 0);  // reach[j]: ancestors of j
+        std::vector<cudaGraphNode_t> deps;
+        for (uint32_t j = 0; j < n; ++j) {
+            const TaskRec &rj = c->h_ring[(size_t)s * c->C + ((ss.flushed + j) & (c->C - 1))];
+            uint64_t *rr = &reach[(size_t)j * words];
+            deps.clear();
+            // scan predecessors latest first; skip those already implied
+            for (int64_t i = (int64_t)j - 1; i >= 0; --i) {
+                if ((rr[i >> 6] >> (i & 63)) & 1u) continue;
+                const TaskRec &ri = c->h_ring[(size_t)s * c->C + ((ss.flushed + i) & (c->C - 1))];
+                if (!recs_conflict(ri, rj)) continue;
+                deps.push_back(nodes[i]);
+                const uint64_t *ra = &reach[(size_t)i * words];
+                for (uint32_t w = 0; w < words; ++w) rr[w] |= ra[w];
+                rr[i >> 6] |= 1ull << (i & 63);
+            }
+            TaskHdr h;
+            std::memcpy(&h, &rj, sizeof h);
+            void *args[] = {&h};
+            kp.gridDim = dim3(rj.ncta);
+            kp.kernelParams = args;
+            e = cudaGraphAddKernelNode(&nodes[j], g, deps.empty() ? nullptr : deps.data(), deps.size(), &kp);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_fail(c, e);
+            }
+            c->stats.graph_edges += deps.size();
+        }
+    }
+    auto t1 = clk::now();
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    auto t2 = clk::now();
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e);
+    }
+    c->stats.graph_build_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    c->stats.graph_instantiate_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
+    c->graphs_pending.push_back(g);
+    c->execs_pending.push_back(x);
+    c->last_exec = x;
+    const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
+    TimedLaunch t{};
+    if (timing) {
+        t = get_events(c);
+        cudaEventRecord(t.a, c->stream);
+    }
+    e = cudaGraphLaunch(x, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (timing) {
+        cudaEventRecord(t.b, c->stream);
+        c->timed.push_back(t);
+    }
+    c->stats.launches++;
+    return ACS_OK;
+}
+
+void release_graphs(acs_ctx *c, bool keep_last) {
+    // everything launched has completed when this is called
+    for (size_t i = 0; i < c->execs_pending.size(); ++i) {
+        if (keep_last && c->execs_pending[i] == c->last_exec) continue;
+        cudaGraphExecDestroy(c->execs_pending[i]);
+        cudaGraphDestroy(c->graphs_pending[i]);
+    }
+    if (keep_last && c->last_exec) {
+        for (size_t i = 0; i < c->execs_pending.size(); ++i) {
+            if (c->execs_pending[i] == c->last_exec) {
+                cudaGraphExec_t x = c->execs_pending[i];
+                cudaGraph_t g = c->graphs_pending[i];
+                c->execs_pending.assign(1, x);
+                c->graphs_pending.assign(1, g);
+                return;
+            }
+        }
+    }
+    c->execs_pending.clear();
+    c->graphs_pending.clear();
+    if (!keep_last) c->last_exec = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+void acs_config_default(acs_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->mode = ACS_MODE_WINDOW;
+    cfg->n_streams = 1;
+    cfg->capacity = 8192;
+    cfg->timeout_ns = 5000000000ull;
+    cfg->device = -1;
+}
+
+const char *acs_strerror(int code) {
+    switch (code) {
+    case ACS_OK: return "ok";
+    case ACS_ERR_INVALID: return "invalid argument";
+    case ACS_ERR_FULL: return "stream ring full (flush and sync, then retry)";
+    case ACS_ERR_TIMEOUT: return "a bounded device wait made no progress before the timeout";
+    case ACS_ERR_DEVICE: return "CUDA runtime error";
+    case ACS_ERR_STOPPED: return "context stopped";
+    case ACS_ERR_ORDER: return "task_id not strictly increasing within its stream";
+    case ACS_ERR_NOMEM: return "out of memory";
+    default: return "unknown status";
+    }
+}
+
+int acs_error(const acs_ctx *ctx) { return ctx ? ctx->err : ACS_ERR_INVALID; }
+
+void acs_destroy(acs_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release_graphs(c, false);
+    for (auto &t : c->timed) c->event_pool.push_back(t);
+    for (auto &t : c->event_pool) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    cudaFree(c->d_ring);
+    cudaFree(c->d_ctl);
+    cudaFree(c->d_done);
+    cudaFree(c->d_remaining);
+    cudaFree(c->d_cells);
+    cudaFree(c->d_log_mask);
+    cudaFree(c->d_log_start);
+    cudaFree(c->d_log_retire);
+    cudaFree(c->d_sched_stats);
+    if (c->h_ring) cudaFreeHost(c->h_ring);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
+    if (!out) return ACS_ERR_INVALID;
+    acs_config cfg;
+    acs_config_default(&cfg);
+    if (cfg_in) {
+        cfg = *cfg_in;
+        for (uint32_t r : cfg.reserved)
+            if (r) return ACS_ERR_INVALID;
+        if (!cfg.n_streams) cfg.n_streams = 1;
+        if (!cfg.capacity) cfg.capacity = 8192;
+        if (!cfg.timeout_ns) cfg.timeout_ns = 5000000000ull;
+    }
+    if (window < 1 || window > (uint32_t)kMaxWindow) return ACS_ERR_INVALID;
+    if (cfg.n_streams > ACS_MAX_STREAMS) return ACS_ERR_INVALID;
+    if (cfg.mode > ACS_MODE_GRAPH) return ACS_ERR_INVALID;
+    if (cfg.capacity > (1u << 24)) return ACS_ERR_INVALID;
+
+    acs_ctx *c = new (std::nothrow) acs_ctx();
+    if (!c) return ACS_ERR_NOMEM;
+    c->cfg = cfg;
+    c->W = window;
+    c->S = cfg.n_streams;
+    uint32_t cap = std::max<uint32_t>(cfg.capacity, kMinCapacity);
+    cap = std::max<uint32_t>(cap, 2u * window + kPrefetch);
+    c->cap_log2 = log2_pow2(cap);
+    c->C = 1u << c->cap_log2;
+    if ((uint64_t)c->S * c->C > (1ull << 24)) {  // work-ring payload holds a 24-bit descriptor index
+        delete c;
+        return ACS_ERR_INVALID;
+    }
+    uint32_t lc = cfg.log_capacity ? cfg.log_capacity : c->C;
+    c->log_log2 = log2_pow2(std::max<uint32_t>(lc, 64));
+    c->LC = 1u << c->log_log2;
+    c->st.resize(c->S);
+
+    cudaError_t e;
+    if (cfg.device >= 0) {
+        e = cudaSetDevice(cfg.device);
+        if (e != cudaSuccess) { delete c; return ACS_ERR_DEVICE; }
+    }
+    cudaGetDevice(&c->device);
+    int rc = ACS_OK;
+    auto chk = [&](cudaError_t e2) {
+        if (e2 != cudaSuccess && rc == ACS_OK) rc = (e2 == cudaErrorMemoryAllocation) ? ACS_ERR_NOMEM : ACS_ERR_DEVICE;
+    };
+    if (cfg.cuda_stream) {
+        c->stream = (cudaStream_t)cfg.cuda_stream;
+    } else {
+        chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const size_t nrec = (size_t)c->S * c->C;
+    chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocDefault));
+    chk(cudaMalloc(&c->d_ring, nrec * sizeof(TaskRec)));
+    chk(cudaMalloc(&c->d_ctl, sizeof(DevCtl)));
+    const uint32_t nslots = c->S * kMaxWindow;
+    chk(cudaMalloc(&c->d_done, nslots * sizeof(uint32_t)));
+    chk(cudaMalloc(&c->d_remaining, nslots * sizeof(uint32_t)));
+    // work ring: at most (2W - 1) * ACS_MAX_NCTA units of one stream are in flight
+    uint32_t cells = 1;
+    while (cells < std::min<uint32_t>(2u * window * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
+    c->ncells = std::max<uint32_t>(cells, 4096);
+    chk(cudaMalloc(&c->d_cells, (size_t)c->ncells * sizeof(unsigned long long)));
+    const size_t nlog = (cfg.flags & ACS_FLAG_LOG) ? (size_t)c->S * c->LC : 1;
+    if (!(cfg.flags & ACS_FLAG_LOG)) c->log_log2 = 0, c->LC = 1;
+    chk(cudaMalloc(&c->d_log_mask, nlog * sizeof(unsigned long long)));
+    chk(cudaMalloc(&c->d_log_start, nlog * sizeof(unsigned long long)));
+    chk(cudaMalloc(&c->d_log_retire, nlog * sizeof(unsigned long long)));
+    chk(cudaMalloc(&c->d_sched_stats, c->S * sizeof(SchedStats)));
+    chk(cudaHostAlloc(&c->h_status, sizeof(HostStatus), cudaHostAllocMapped));
+    if (rc) { acs_destroy(c); return rc; }
+    std::memset((void *)c->h_status, 0, sizeof(HostStatus));
+    chk(cudaHostGetDevicePointer((void **)&c->d_status, (void *)c->h_status, 0));
+    chk(cudaMemsetAsync(c->d_sched_stats, 0, c->S * sizeof(SchedStats), c->stream));
+    chk(cudaMemsetAsync(c->d_log_mask, 0, nlog * sizeof(unsigned long long), c->stream));
+    chk(launch_init(c->d_cells, c->ncells, c->d_ctl, c->d_done, c->d_remaining, nslots, c->stream));
+
+    // grid: one scheduler CTA per stream + worker CTAs, all co-resident
+    c->smem = dyn_smem_bytes(window);
+    const void *kfn = persistent_kernel_fn();
+    chk(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+    int per_sm = 0, sms = 0;
+    chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, c->smem));
+    chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    chk(cudaStreamSynchronize(c->stream));
+    if (rc) { acs_destroy(c); return rc; }
+    const uint32_t max_grid = (uint32_t)per_sm * (uint32_t)sms;
+    if (cfg.mode == ACS_MODE_WINDOW && max_grid <= c->S) { acs_destroy(c); return ACS_ERR_INVALID; }
+    uint32_t slots = cfg.cta_slots ? cfg.cta_slots : (max_grid > c->S ? max_grid - c->S : 0);
+    if (cfg.mode == ACS_MODE_WINDOW && (slots == 0 || slots + c->S > max_grid)) { acs_destroy(c); return ACS_ERR_INVALID; }
+    c->cta_slots = slots;
+    c->grid = slots + c->S;
+    c->stats.cta_slots = c->cta_slots;
+    c->stats.grid = c->grid;
+    *out = c;
+    return ACS_OK;
+}
+
+int acs_get_addresses(const acs_args *a, acs_segment *r, uint32_t *nr, acs_segment *w, uint32_t *nw) {
+    if (!a || !r || !nr || !w || !nw) return ACS_ERR_INVALID;
+    uint32_t R = 0, Wn = 0;
+    auto rd = [&](uint64_t p, uint64_t n) { r[R++] = acs_segment{p, n}; };
+    auto wr = [&](uint64_t p, uint64_t n) { w[Wn++] = acs_segment{p, n}; };
+    const uint64_t F = 4, S = ACS_RL_SPHERES;
+    switch (a->op) {
+    case ACS_OP_NOP: break;
+    case ACS_OP_AXPY: {
+        acs_axpy_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.x, x.n * F); rd(x.y, x.n * F); wr(x.y, x.n * F);
+        break;
+    }
+    case ACS_OP_SCALE: {
+        acs_axpy_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.x, x.n * F); wr(x.y, x.n * F);
+        break;
+    }
+    case ACS_OP_ADD: {
+        acs_add_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.x, x.n * F); rd(x.y, x.n * F); wr(x.z, x.n * F);
+        break;
+    }
+    case ACS_OP_GEMV: {  // reads W (m*k) and x (k), writes y (m): Fig. get_addresses with k = 1 column
+        acs_gemv_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.W, (uint64_t)x.m * x.k * F); rd(x.x, x.k * F); wr(x.y, x.m * F);
+        break;
+    }
+    case ACS_OP_BIAS_RELU: {
+        acs_bias_relu_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.t, x.n * F); rd(x.b, x.n * F); wr(x.t, x.n * F);
+        break;
+    }
+    case ACS_OP_RESID: {
+        acs_resid_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.h, x.n * F); rd(x.u, x.n * F); rd(x.b, x.n * F); wr(x.h, x.n * F);
+        break;
+    }
+    case ACS_OP_RL_BROADPHASE: {
+        acs_rl_broadphase_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.pos, x.nenv * S * 3 * F); rd(x.prop, x.nenv * S * 2 * F);
+        wr(x.cont, (uint64_t)x.nenv * ACS_RL_REC_BYTES); wr(x.nisl, x.nenv * F);
+        break;
+    }
+    case ACS_OP_RL_SOLVE: {
+        acs_rl_solve_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.pos, S * 3 * F); rd(x.prop, S * 2 * F); rd(x.cont, ACS_RL_REC_BYTES); rd(x.vel, S * 3 * F);
+        wr(x.vel, S * 3 * F);
+        break;
+    }
+    case ACS_OP_RL_INTEGRATE: {
+        acs_rl_integrate_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.pos, x.nenv * S * 3 * F); rd(x.vel, x.nenv * S * 3 * F); rd(x.prop, x.nenv * S * 2 * F);
+        wr(x.pos, x.nenv * S * 3 * F); wr(x.vel, x.nenv * S * 3 * F);
+        break;
+    }
+    case ACS_OP_WAIT_FLAG: {
+        acs_wait_args x; std::memcpy(&x, a->bytes, sizeof x);
+        rd(x.flag, 4);
+        break;
+    }
+    case ACS_OP_SLEEP: {
+        acs_sleep_args x; std::memcpy(&x, a->bytes, sizeof x);
+        wr(x.y, 4);
+        break;
+    }
+    default:
+        return ACS_ERR_INVALID;
+    }
+    *nr = R;
+    *nw = Wn;
+    return ACS_OK;
+}
+
+int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_args *args,
+                      const acs_segment *reads, uint32_t n_reads, const acs_segment *writes, uint32_t n_writes) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    if (!args || stream >= c->S || (n_reads && !reads) || (n_writes && !writes)) return ACS_ERR_INVALID;
+    if (!valid_op(args->op) || args->ncta < 1 || args->ncta > ACS_MAX_NCTA || args->reserved) return ACS_ERR_INVALID;
+    StreamState &ss = c->st[stream];
+    if (ss.has_id && task_id <= ss.last_id) return ACS_ERR_ORDER;
+    if ((uint64_t)ss.submitted + c->W - 1 - ss.synced + 1 > c->C - kPrefetch) return ACS_ERR_FULL;
+    TaskRec &r = c->h_ring[(size_t)stream * c->C + (ss.submitted & (c->C - 1))];
+    uint32_t cnt = 0;
+    uint16_t wmask = 0;
+    uint64_t bytes = 0;
+    if (!add_segs(reads, n_reads, false, r.seg, cnt, wmask, bytes) ||
+        !add_segs(writes, n_writes, true, r.seg, cnt, wmask, bytes))
+        return ACS_ERR_INVALID;
+    r.task_id = task_id;
+    r.op = args->op;
+    r.ncta = args->ncta;
+    r.wmask = wmask;
+    r.nseg = (uint8_t)cnt;
+    r.flags = 0;
+    r.seq = ss.submitted;
+    std::memcpy(r.args, args->bytes, sizeof r.args);
+    ss.has_id = true;
+    ss.last_id = task_id;
+    ss.submitted++;
+    c->stats.tasks_submitted++;
+    c->stats.seg_bytes += bytes;
+    return ACS_OK;
+}
+
+int acs_submit(acs_ctx *c, uint32_t task_id, const acs_args *args, const acs_segment *reads, uint32_t n_reads,
+               const acs_segment *writes, uint32_t n_writes) {
+    return acs_submit_stream(c, 0, task_id, args, reads, n_reads, writes, n_writes);
+}
+
+int acs_submit_ops(acs_ctx *c, uint32_t stream, uint32_t n, const uint32_t *task_ids, const acs_args *args) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    if (n && (!task_ids || !args)) return ACS_ERR_INVALID;
+    acs_segment r[ACS_MAX_SEGS], w[ACS_MAX_SEGS];
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t nr = 0, nw = 0;
+        int rc = acs_get_addresses(&args[i], r, &nr, w, &nw);
+        if (rc) return rc;
+        rc = acs_submit_stream(c, stream, task_ids[i], &args[i], r, nr, w, nw);
+        if (rc) return rc;
+    }
+    return ACS_OK;
+}
+
+int acs_flush(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    uint32_t n = 0;
+    for (auto &s : c->st) n += s.submitted - s.flushed;
+    if (!n) return ACS_OK;
+    int rc;
+    if (c->cfg.mode == ACS_MODE_WINDOW) rc = flush_window(c);
+    else if (c->cfg.mode == ACS_MODE_INORDER) rc = flush_inorder(c);
+    else rc = flush_graph(c);
+    if (rc) return rc;
+    for (auto &s : c->st) {
+        c->stats.tasks_flushed += s.submitted - s.flushed;
+        s.flushed = s.submitted;
+    }
+    return ACS_OK;
+}
+
+int acs_sync(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    collect_timing(c);
+    if (c->cfg.mode == ACS_MODE_WINDOW) {
+        const uint32_t derr = c->h_status->err;
+        if (derr) fail(c, (int)(int32_t)derr);
+    }
+    if (c->cfg.mode == ACS_MODE_GRAPH) release_graphs(c, true);
+    if (c->err) return c->err;
+    for (auto &s : c->st) s.synced = s.flushed;
+    return ACS_OK;
+}
+
+int acs_graph_replay(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    if (c->cfg.mode != ACS_MODE_GRAPH || !c->last_exec) return ACS_ERR_INVALID;
+    const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
+    TimedLaunch t{};
+    if (timing) {
+        t = get_events(c);
+        cudaEventRecord(t.a, c->stream);
+    }
+    cudaError_t e = cudaGraphLaunch(c->last_exec, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (timing) {
+        cudaEventRecord(t.b, c->stream);
+        c->timed.push_back(t);
+    }
+    c->stats.launches++;
+    return ACS_OK;
+}
+
+int acs_get_log(acs_ctx *c, uint32_t stream, uint64_t first, uint32_t n, uint64_t *masks, uint64_t *start,
+                uint64_t *retire) {
+    if (!c || stream >= c->S || !(c->cfg.flags & ACS_FLAG_LOG)) return ACS_ERR_INVALID;
+    const StreamState &ss = c->st[stream];
+    if (first + n > ss.synced || n > c->LC || first + c->LC < ss.synced) return ACS_ERR_INVALID;
+    uint64_t *dst[3] = {masks, start, retire};
+    unsigned long long *src[3] = {c->d_log_mask, c->d_log_start, c->d_log_retire};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        uint64_t a = first, done = 0;
+        while (done < n) {
+            const uint64_t pa = a & (c->LC - 1);
+            const uint64_t m = std::min<uint64_t>(n - done, c->LC - pa);
+            cudaError_t e = cudaMemcpy(dst[k] + done, src[k] + (size_t)stream * c->LC + pa, m * sizeof(uint64_t),
+                                       cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return ACS_ERR_DEVICE;
+            a += m;
+            done += m;
+        }
+    }
+    return ACS_OK;
+}
+
+int acs_get_stats(acs_ctx *c, acs_stats *out) {
+    if (!c || !out) return ACS_ERR_INVALID;
+    if (c->cfg.mode == ACS_MODE_WINDOW) {
+        std::vector<SchedStats> ss(c->S);
+        if (cudaMemcpy(ss.data(), c->d_sched_stats, c->S * sizeof(SchedStats), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            c->stats.sched_cycles = c->stats.sched_busy_cycles = c->stats.sched_inserts = 0;
+            for (auto &x : ss) {
+                c->stats.sched_cycles += x.cycles;
+                c->stats.sched_busy_cycles += x.busy_cycles;
+                c->stats.sched_inserts += x.inserts;
+            }
+        }
+    }
+    *out = c->stats;
+    return ACS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+"""Drive streamgen task streams through libacs (argument marshalling only).
+
+Maps named streamgen buffers to CUDA tensors, packs each task's device
+pointers and scalars into ``acs_args`` rows (the layouts of the acs_*_args
+structs in include/acs.h), submits them with ``acs_submit_ops`` -- which
+derives read/write segments in the library (acs_get_addresses) -- and runs the
+rigid-sphere stream step by step, reading back the island counts its own
+broadphase tasks wrote.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import acs
+
+# per-op argument layouts (must match include/acs.h)
+_U8 = "<u8"
+OP_DTYPES = {
+    "axpy": np.dtype([("x", _U8), ("y", _U8), ("n", "<u4"), ("a", "<f4")]),
+    "scale": np.dtype([("x", _U8), ("y", _U8), ("n", "<u4"), ("a", "<f4")]),
+    "add": np.dtype([("x", _U8), ("y", _U8), ("z", _U8), ("n", "<u4"), ("pad", "<u4")]),
+    "gemv": np.dtype([("W", _U8), ("x", _U8), ("y", _U8), ("m", "<u4"), ("k", "<u4")]),
+    "bias_relu": np.dtype([("t", _U8), ("b", _U8), ("n", "<u4"), ("pad", "<u4")]),
+    "resid": np.dtype([("h", _U8), ("u", _U8), ("b", _U8), ("n", "<u4"), ("pad", "<u4")]),
+    "rl_broadphase": np.dtype([("pos", _U8), ("prop", _U8), ("cont", _U8), ("nisl", _U8), ("nenv", "<u4"),
+                               ("pad", "<u4")]),
+    "rl_solve": np.dtype([("pos", _U8), ("prop", _U8), ("cont", _U8), ("vel", _U8), ("beta_dt", "<f4"),
+                          ("slop", "<f4")]),
+    "rl_integrate": np.dtype([("pos", _U8), ("vel", _U8), ("prop", _U8), ("nenv", "<u4"), ("dt", "<f4"),
+                              ("gdt", "<f4"), ("box", "<f4")]),
+    "wait_flag": np.dtype([("flag", _U8), ("limit_ns", _U8)]),
+    "sleep": np.dtype([("y", _U8), ("ns", _U8), ("tag", "<f4"), ("pad", "<u4")]),
+}
+for _dt in OP_DTYPES.values():
+    assert _dt.itemsize <= 48
+
+
+class DeviceBuffers:
+    """Named streamgen buffers as CUDA byte tensors (caller-owned device memory)."""
+
+    def __init__(self, buffers: Dict[str, np.ndarray], device: str = "cuda"):
+        self.dtype = {k: v.dtype for k, v in buffers.items()}
+        self.t = {k: torch.from_numpy(np.ascontiguousarray(v).view(np.uint8).copy()).to(device)
+                  for k, v in buffers.items()}
+        self.base = {k: int(v.data_ptr()) for k, v in self.t.items()}
+
+    def ptr(self, ref) -> int:
+        return self.base[ref.buf] + ref.off * self.dtype[ref.buf].itemsize
+
+    def upload(self, buffers: Dict[str, np.ndarray]) -> None:
+        for k, v in buffers.items():
+            self.t[k].copy_(torch.from_numpy(np.ascontiguousarray(v).view(np.uint8)))
+
+    def download(self) -> Dict[str, np.ndarray]:
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy().view(self.dtype[k]) for k, v in self.t.items()}
+
+
+def _args_row(op: str, ncta: int, fields: dict) -> np.ndarray:
+    row = np.zeros(1, acs.ARGS_DTYPE)
+    row["op"] = acs.OPS[op]
+    row["ncta"] = ncta
+    body = np.zeros(1, OP_DTYPES[op])
+    for k, v in fields.items():
+        body[k] = v
+    raw = np.zeros(48, np.uint8)
+    raw[:body.itemsize] = np.frombuffer(body.tobytes(), np.uint8)
+    row["bytes"] = raw.tobytes()
+    return row
+
+
+def pack_task(task, bufs: DeviceBuffers) -> np.ndarray:
+    """One streamgen task as a packed acs_args row."""
+    A, S = task.arrays, task.scalars
+    op = task.op
+    if op in ("axpy", "scale"):
+        f = {"x": bufs.ptr(A["x"]), "y": bufs.ptr(A["y"]), "n": A["y"].n, "a": S["a"]}
+    elif op == "add":
+        f = {"x": bufs.ptr(A["x"]), "y": bufs.ptr(A["y"]), "z": bufs.ptr(A["z"]), "n": A["z"].n}
+    elif op == "gemv":
+        f = {"W": bufs.ptr(A["W"]), "x": bufs.ptr(A["x"]), "y": bufs.ptr(A["y"]), "m": S["m"], "k": S["k"]}
+    elif op == "bias_relu":
+        f = {"t": bufs.ptr(A["t"]), "b": bufs.ptr(A["b"]), "n": A["t"].n}
+    elif op == "resid":
+        f = {"h": bufs.ptr(A["h"]), "u": bufs.ptr(A["u"]), "b": bufs.ptr(A["b"]), "n": A["h"].n}
+    elif op == "rl_broadphase":
+        f = {"pos": bufs.ptr(A["pos"]), "prop": bufs.ptr(A["prop"]), "cont": bufs.ptr(A["cont"]),
+             "nisl": bufs.ptr(A["nisl"]), "nenv": S["nenv"]}
+    elif op == "rl_solve":
+        f = {"pos": bufs.ptr(A["pos"]), "prop": bufs.ptr(A["prop"]), "cont": bufs.ptr(A["cont"]),
+             "vel": bufs.ptr(A["vel"]), "beta_dt": S["beta_dt"], "slop": S["slop"]}
+    elif op == "rl_integrate":
+        f = {"pos": bufs.ptr(A["pos"]), "vel": bufs.ptr(A["vel"]), "prop": bufs.ptr(A["prop"]),
+             "nenv": S["nenv"], "dt": S["dt"], "gdt": S["gdt"], "box": S["box"]}
+    elif op == "sleep":
+        f = {"y": bufs.ptr(A["y"]), "ns": S["ns"], "tag": S["tag"]}
+    elif op == "wait_flag":
+        f = {"flag": S["flag"], "limit_ns": S["limit_ns"]}
+    else:
+        raise ValueError(f"unknown op {op!r}")
+    return _args_row(op, task.ncta, f)
+
+
+def pack_tasks(tasks, bufs: DeviceBuffers):
+    """(task_ids, packed acs_args rows) for a list of streamgen tasks."""
+    if not tasks:
+        return np.zeros(0, np.uint32), np.zeros(0, acs.ARGS_DTYPE)
+    ids = np.array([t.task_id for t in tasks], np.uint32)
+    return ids, np.concatenate([pack_task(t, bufs) for t in tasks])
+
+
+MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph": acs.ACS_MODE_GRAPH}
+
+
+class Context:
+    """An acs_ctx on the current torch CUDA stream (raises on every error)."""
+
+    def __init__(self, window: int, mode: str = "window", n_streams: int = 1, cta_slots: int = 0,
+                 capacity: int = 0, log: bool = False, timing: bool = False, timeout_s: float = 5.0,
+                 cuda_stream: Optional[int] = None):
+        cfg = acs.acs_config_default()
+        cfg.mode = MODES[mode]
+        cfg.n_streams = n_streams
+        cfg.cta_slots = cta_slots
+        if capacity:
+            cfg.capacity = capacity
+        cfg.flags = (acs.ACS_FLAG_LOG if log else 0) | (acs.ACS_FLAG_TIMING if timing else 0)
+        cfg.timeout_ns = int(timeout_s * 1e9)
+        cfg.cuda_stream = C.c_void_p(cuda_stream if cuda_stream is not None
+                                     else torch.cuda.current_stream().cuda_stream)
+        self.window, self.mode, self.n_streams = window, mode, n_streams
+        self.h = acs.acs_init(window, cfg)
+
+    def submit_packed(self, ids: np.ndarray, packed: np.ndarray, stream: int = 0) -> None:
+        acs.check(acs.acs_submit_ops(self.h, stream, ids, packed), "acs_submit_ops")
+
+    def submit(self, tasks, bufs: DeviceBuffers, stream: int = 0) -> None:
+        self.submit_packed(*pack_tasks(tasks, bufs), stream=stream)
+
+    def flush(self) -> None:
+        acs.check(acs.acs_flush(self.h), "acs_flush")
+
+    def sync(self) -> None:
+        acs.check(acs.acs_sync(self.h), "acs_sync")
+
+    def sync_code(self) -> int:
+        return acs.acs_sync(self.h)
+
+    def log(self, stream: int, first: int, n: int):
+        return acs.acs_get_log(self.h, stream, first, n)
+
+    def stats(self) -> dict:
+        return acs.stats_dict(acs.acs_get_stats(self.h))
+
+    def replay(self) -> None:
+        acs.check(acs.acs_graph_replay(self.h), "acs_graph_replay")
+
+    def close(self) -> None:
+        if self.h:
+            acs.acs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def run_stream(stream, mode: str = "window", window: Optional[int] = None, log: bool = False,
+               cta_slots: int = 0, flush_every: int = 0):
+    """Run one streamgen Stream on the GPU; returns (buffers after, context
+    stats, log or None). ``flush_every`` > 0 splits the stream into flushes."""
+    bufs = DeviceBuffers(stream.buffers)
+    W = window or stream.window
+    with Context(W, mode=mode, log=log, cta_slots=cta_slots) as ctx:
+        ids, packed = pack_tasks(stream.tasks, bufs)
+        step = flush_every or len(ids) or 1
+        for a in range(0, len(ids), step):
+            ctx.submit_packed(ids[a:a + step], packed[a:a + step])
+            ctx.flush()
+        ctx.sync()
+        lg = ctx.log(0, 0, len(ids)) if (log and mode == "window") else None
+        st = ctx.stats()
+    return bufs.download(), st, lg
+
+
+# ---- rigid-sphere stream -------------------------------------------------------------
+
+class RLDriver:
+    """Runs a streamgen.RLSim on the GPU through one Context: per step, flush
+    the batch, sync, read back nisl (4 bytes per env) and emit the next plan.
+    Packing is vectorised from per-env / per-chunk templates."""
+
+    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context):
+        self.sim, self.bufs, self.ctx = sim, bufs, ctx
+        p = sim.p
+        sc = sim.scalars()
+        self.templates = {}
+        for kind, op in ((0, "rl_broadphase"), (1, "rl_solve"), (2, "rl_integrate")):
+            n = p.n_env if kind == 1 else p.n_env // p.chunk
+            rows = []
+            for idx in range(n):
+                fake = sim.tasks(_one_plan(kind, idx))[0]
+                fake.scalars = dict(sc[op])
+                rows.append(pack_task(fake, bufs))
+            self.templates[kind] = np.concatenate(rows)
+        self.nisl_host = torch.empty(p.n_env, dtype=torch.int32, pin_memory=True)
+
+    def pack(self, plan):
+        rows = np.empty(len(plan.kind), acs.ARGS_DTYPE)
+        for kind in (0, 1, 2):
+            sel = plan.kind == kind
+            if sel.any():
+                rows[sel] = self.templates[kind][plan.index[sel]]
+        rows["ncta"] = plan.ncta
+        return plan.ids, rows
+
+    def read_nisl(self) -> np.ndarray:
+        self.nisl_host.copy_(self.bufs.t["nisl"].view(torch.int32), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return self.nisl_host.numpy().view(np.uint32)
+
+    def run(self, record_plans: bool = False) -> List:
+        plans = []
+        plan = self.sim.first_plan()
+        for t in range(self.sim.p.steps + 1):
+            if t > 0:
+                plan = self.sim.step_plan(t - 1, self.read_nisl())
+            self.ctx.submit_packed(*self.pack(plan))
+            self.ctx.flush()
+            self.ctx.sync()
+            if record_plans:
+                plans.append(plan)
+        return plans
+
+
+def _one_plan(kind: int, idx: int):
+    import streamgen as sg
+    return sg.RLPlan(np.array([kind], np.uint8), np.array([idx], np.uint32), np.array([1], np.uint16), 0,
+                     np.array([0], np.uint32))

@@ -247,53 +247,91 @@ class RLSim:
                 Ref("prop", e0 * S * 2, ne * S * 2), Ref("cont", e0 * RL_REC_BYTES, ne * RL_REC_BYTES),
                 Ref("nisl", e0, ne))
 
-    def _emit(self, op, ncta, arrays, scalars=None) -> Task:
-        t = Task(self.next_id, op, int(ncta), arrays, scalars or {})
-        self.next_id += 1
-        return t
+    # -- emission plans ----------------------------------------------------------
+    # A plan lists the tasks of one batch in program order as three arrays:
+    # kind (0 broadphase of a chunk, 1 solve of an env, 2 integrate of a chunk),
+    # index (chunk or env) and ncta, plus the step whose scalars they use.
+    KIND_BROADPHASE, KIND_SOLVE, KIND_INTEGRATE = 0, 1, 2
 
-    def _broadphase(self, step: int) -> List[Task]:
-        p, out = self.p, []
-        for c in range(p.n_env // p.chunk):
-            pos, _, prop, cont, nisl = self._refs_env(c * p.chunk, p.chunk)
-            out.append(self._emit("rl_broadphase", self._chunk_ncta(0, step, c),
-                                  {"pos": pos, "prop": prop, "cont": cont, "nisl": nisl},
-                                  {"nenv": np.uint32(p.chunk)}))
+    def _chunks(self) -> np.ndarray:
+        return np.arange(self.p.n_env // self.p.chunk, dtype=np.uint32)
+
+    def _chunk_nctas(self, kind: int, step: int) -> np.ndarray:
+        return np.array([self._chunk_ncta(kind, step, int(c)) for c in self._chunks()], np.uint16)
+
+    def first_plan(self) -> "RLPlan":
+        ch = self._chunks()
+        return self._ids(RLPlan(np.zeros(len(ch), np.uint8), ch, self._chunk_nctas(0, 0), 0))
+
+    def step_plan(self, step: int, nisl: np.ndarray) -> "RLPlan":
+        """Solve + integrate of ``step`` and broadphase of ``step + 1``."""
+        p = self.p
+        nisl = np.asarray(nisl).reshape(-1).astype(np.int64)
+        if nisl.shape[0] != p.n_env:
+            raise ValueError("nisl must hold one count per environment")
+        envs = np.nonzero(nisl > 0)[0].astype(np.uint32)
+        solve_ncta = np.clip(nisl[envs], 1, p.max_solve_ncta).astype(np.uint16)
+        ch = self._chunks()
+        kinds = [np.full(len(envs), 1, np.uint8), np.full(len(ch), 2, np.uint8)]
+        index = [envs, ch]
+        ncta = [solve_ncta, self._chunk_nctas(1, step)]
+        if step + 1 < p.steps:
+            kinds.append(np.zeros(len(ch), np.uint8))
+            index.append(ch)
+            ncta.append(self._chunk_nctas(0, step + 1))
+        return self._ids(RLPlan(np.concatenate(kinds), np.concatenate(index), np.concatenate(ncta), step))
+
+    def _ids(self, plan: "RLPlan") -> "RLPlan":
+        plan.ids = np.arange(self.next_id, self.next_id + len(plan.kind), dtype=np.uint32)
+        self.next_id += len(plan.kind)
+        return plan
+
+    def scalars(self) -> Dict[str, Dict[str, object]]:
+        """Scalar arguments of each task kind (the same every step)."""
+        p, f32 = self.p, np.float32
+        dt = f32(p.dt)
+        return {"rl_broadphase": {"nenv": np.uint32(p.chunk)},
+                "rl_solve": {"beta_dt": f32(f32(p.beta) / dt), "slop": f32(p.slop)},
+                "rl_integrate": {"nenv": np.uint32(p.chunk), "dt": dt, "gdt": f32(f32(p.gravity) * dt),
+                                 "box": f32(p.box)}}
+
+    def tasks(self, plan: "RLPlan") -> List[Task]:
+        """The plan as streamgen tasks."""
+        p, sc, out = self.p, self.scalars(), []
+        for tid, kind, idx, nc in zip(plan.ids, plan.kind, plan.index, plan.ncta):
+            idx = int(idx)
+            if kind == 1:
+                pos, vel, prop, cont, _ = self._refs_env(idx, 1)
+                out.append(Task(int(tid), "rl_solve", int(nc),
+                                {"pos": pos, "vel": vel, "prop": prop, "cont": cont}, dict(sc["rl_solve"])))
+            else:
+                pos, vel, prop, cont, nisl = self._refs_env(idx * p.chunk, p.chunk)
+                if kind == 0:
+                    out.append(Task(int(tid), "rl_broadphase", int(nc),
+                                    {"pos": pos, "prop": prop, "cont": cont, "nisl": nisl},
+                                    dict(sc["rl_broadphase"])))
+                else:
+                    out.append(Task(int(tid), "rl_integrate", int(nc), {"pos": pos, "vel": vel, "prop": prop},
+                                    dict(sc["rl_integrate"])))
         return out
 
-    # -- batches -------------------------------------------------------------------
+    # -- batches ---------------------------------------------------------------------
     def first_batch(self) -> List[Task]:
         """Broadphase of step 0."""
-        return self._broadphase(0)
+        return self.tasks(self.first_plan())
 
     def step_batch(self, step: int, nisl: np.ndarray) -> List[Task]:
         """Solve + integrate of ``step`` and broadphase of ``step + 1``."""
-        p = self.p
-        nisl = np.asarray(nisl).reshape(-1)
-        if nisl.shape[0] != p.n_env:
-            raise ValueError("nisl must hold one count per environment")
-        out = []
-        f32 = np.float32
-        beta_dt = f32(f32(p.beta) / f32(p.dt))
-        for e in range(p.n_env):
-            k = int(nisl[e])
-            if k <= 0:
-                continue
-            pos, vel, prop, cont, _ = self._refs_env(e, 1)
-            out.append(self._emit("rl_solve", min(max(k, 1), p.max_solve_ncta),
-                                  {"pos": pos, "vel": vel, "prop": prop, "cont": cont},
-                                  {"beta_dt": beta_dt, "slop": f32(p.slop)}))
-        dt = f32(p.dt)
-        gdt = f32(f32(p.gravity) * dt)
-        for c in range(p.n_env // p.chunk):
-            pos, vel, prop, _, _ = self._refs_env(c * p.chunk, p.chunk)
-            out.append(self._emit("rl_integrate", self._chunk_ncta(1, step, c),
-                                  {"pos": pos, "vel": vel, "prop": prop},
-                                  {"nenv": np.uint32(p.chunk), "dt": dt, "gdt": gdt,
-                                   "box": f32(p.box)}))
-        if step + 1 < p.steps:
-            out.extend(self._broadphase(step + 1))
-        return out
+        return self.tasks(self.step_plan(step, nisl))
+
+
+@dataclass
+class RLPlan:
+    kind: np.ndarray
+    index: np.ndarray
+    ncta: np.ndarray
+    step: int
+    ids: Optional[np.ndarray] = None
 
 
 # ----------------------------------------------------------------------------

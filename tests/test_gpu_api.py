@@ -1,0 +1,161 @@
+"""C-ABI behaviour on the GPU: argument validation, sticky errors, bounded
+waits that end in ACS_ERR_TIMEOUT with the device still usable, explicit
+segments including the whole-memory segment, and independent streams."""
+import ctypes as C
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import streamgen as sg
+from oracle import addresses, deps, execute
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2401_12377_b300 import build
+    build.build()
+    from paper_2401_12377_b300 import acs, harness
+
+
+def _nop_args(ncta=1):
+    a = acs.acs_args()
+    a.op = acs.OPS["nop"]
+    a.ncta = ncta
+    return a
+
+
+def test_submit_validation():
+    with harness.Context(8) as ctx:
+        h = ctx.h
+        a = _nop_args()
+        seg = [(4096, 16)]
+        assert acs.acs_submit(h, 1, a, seg, seg) == acs.ACS_OK
+        assert acs.acs_submit(h, 1, a, seg, seg) == acs.ACS_ERR_ORDER       # not increasing
+        assert acs.acs_submit(h, 0, a, seg, seg) == acs.ACS_ERR_ORDER
+        assert acs.acs_submit(h, 2, a, [(4096, 16)] * 17, []) == acs.ACS_ERR_INVALID   # > 16 segments
+        assert acs.acs_submit(h, 2, a, [(4096, 0)] * 20, []) == acs.ACS_OK             # empty ones dropped
+        assert acs.acs_submit(h, 3, a, [((1 << 64) - 8, 16)], []) == acs.ACS_ERR_INVALID  # wraps 2^64
+        assert acs.acs_submit(h, 3, a, [((1 << 64) - 16, 16)], []) == acs.ACS_OK          # ends at 2^64
+        assert acs.acs_submit(h, 4, a, [acs.ACS_WHOLE_MEMORY], []) == acs.ACS_OK
+        bad = _nop_args(0)
+        assert acs.acs_submit(h, 5, bad, [], []) == acs.ACS_ERR_INVALID
+        bad = _nop_args(257)
+        assert acs.acs_submit(h, 5, bad, [], []) == acs.ACS_ERR_INVALID
+        bad = _nop_args(); bad.op = 99
+        assert acs.acs_submit(h, 5, bad, [], []) == acs.ACS_ERR_INVALID
+        assert acs.acs_submit_stream(h, 1, 5, a, [], []) == acs.ACS_ERR_INVALID   # only stream 0
+        ctx.flush()
+        ctx.sync()
+
+
+def test_ring_full_until_sync():
+    with harness.Context(8, capacity=64) as ctx:
+        a = _nop_args()
+        n = 0
+        while acs.acs_submit(ctx.h, n, a, [], [(4096, 4)]) == acs.ACS_OK:
+            n += 1
+            assert n < 64
+        assert acs.acs_submit(ctx.h, n, a, [], [(4096, 4)]) == acs.ACS_ERR_FULL
+        ctx.flush()
+        ctx.sync()
+        assert acs.acs_submit(ctx.h, n, a, [], [(4096, 4)]) == acs.ACS_OK       # room again
+        ctx.flush()
+        ctx.sync()
+
+
+def test_timeout_is_bounded_sticky_and_leaves_the_device_usable():
+    flag = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with harness.Context(8, timeout_s=0.2) as ctx:
+        row = harness._args_row("wait_flag", 1, {"flag": flag.data_ptr(), "limit_ns": 3_000_000_000})
+        ctx.submit_packed(np.array([0], np.uint32), row)
+        t0 = time.time()
+        ctx.flush()
+        code = ctx.sync_code()
+        dt = time.time() - t0
+        assert code == acs.ACS_ERR_TIMEOUT, acs.acs_strerror(code)
+        assert dt < 2.5
+        assert acs.acs_error(ctx.h) == acs.ACS_ERR_TIMEOUT                  # sticky
+        assert acs.acs_submit(ctx.h, 1, _nop_args(), [], []) == acs.ACS_ERR_TIMEOUT
+    # the device is healthy: a fresh context runs a stream correctly
+    s = sg.elementwise_stream(1, n_tasks=16)
+    out, _, _ = harness.run_stream(s)
+    ref = execute.run_inorder(s.buffers, s.tasks)
+    assert all(np.array_equal(out[k], ref[k]) for k in ref)
+
+
+def test_wait_flag_released_by_the_host_completes():
+    flag = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with harness.Context(8, timeout_s=5) as ctx:
+        row = harness._args_row("wait_flag", 1, {"flag": flag.data_ptr(), "limit_ns": 3_000_000_000})
+        ctx.submit_packed(np.array([0], np.uint32), row)
+        ctx.flush()
+        side = torch.cuda.Stream()
+        time.sleep(0.05)
+        with torch.cuda.stream(side):
+            flag.fill_(1)
+        ctx.sync()
+
+
+def _explicit_stream(seed):
+    """Elementwise tasks plus NOP tasks with hand-given segments, including the
+    whole-memory segment (indirect access, Sec. IV-A)."""
+    s = sg.elementwise_stream(seed, n_tasks=40)
+    return s
+
+
+def test_whole_memory_segment_orders_everything():
+    s = sg.elementwise_stream(31, n_tasks=30)
+    bufs = harness.DeviceBuffers(s.buffers)
+    ids, packed = harness.pack_tasks(s.tasks, bufs)
+    W = 8
+    wild_at = {7: "read", 15: "write"}
+    # oracle segments with the wildcard tasks inserted
+    lay = addresses.Layout(s.buffers)
+    segs, n = [], 0
+    with harness.Context(W, log=True) as ctx:
+        tid = 0
+        for i in range(len(ids)):
+            if i in wild_at:
+                kind = wild_at[i]
+                rd = [deps.WHOLE_MEMORY] if kind == "read" else []
+                wr = [deps.WHOLE_MEMORY] if kind == "write" else []
+                segs.append((rd, wr))
+                rc = acs.acs_submit(ctx.h, tid, _nop_args(), [acs.ACS_WHOLE_MEMORY] if rd else [],
+                                    [acs.ACS_WHOLE_MEMORY] if wr else [])
+                assert rc == acs.ACS_OK
+                tid += 1
+            segs.append(addresses.task_segments(s.tasks[i], lay))
+            ctx.submit_packed(np.array([tid], np.uint32), packed[i:i + 1])
+            tid += 1
+        ctx.flush()
+        ctx.sync()
+        masks, start, retire = ctx.log(0, 0, tid)
+    E = deps.full_dag(segs)
+    D = deps.window_dag(E, W)
+    assert deps.edges_from_masks([int(m) for m in masks], W) == D
+    assert not deps.check_legal(E, [int(x) for x in start], [int(x) for x in retire])
+    out = bufs.download()
+    ref = execute.run_inorder(s.buffers, s.tasks)
+    assert all(np.array_equal(out[k], ref[k]) for k in ref)
+
+
+def test_independent_streams_in_one_launch():
+    streams = [sg.elementwise_stream(50 + i, n_tasks=20 + 13 * i, ranges=bool(i % 2)) for i in range(5)]
+    bufs = [harness.DeviceBuffers(s.buffers) for s in streams]
+    with harness.Context(8, n_streams=5, log=True) as ctx:
+        for i, s in enumerate(streams):
+            ctx.submit(s.tasks, bufs[i], stream=i)
+        ctx.flush()
+        ctx.sync()
+        for i, s in enumerate(streams):
+            segs = addresses.stream_segments(s.tasks, s.buffers)
+            E = deps.full_dag(segs)
+            masks, start, retire = ctx.log(i, 0, len(s.tasks))
+            assert deps.edges_from_masks([int(m) for m in masks], 8) == deps.window_dag(E, 8)
+            assert not deps.check_legal(E, [int(x) for x in start], [int(x) for x in retire])
+            ref = execute.run_inorder(s.buffers, s.tasks)
+            out = bufs[i].download()
+            assert all(np.array_equal(out[k], ref[k]) for k in ref)
+        assert ctx.stats()["launches"] == 1
