@@ -131,7 +131,8 @@ enum acs_mode {
 enum acs_flags {
     ACS_FLAG_LOG = 1,      /* record per-task upstream-candidate masks and
                               start / retire tickets (window mode) */
-    ACS_FLAG_TIMING = 2    /* time each device launch with CUDA events */
+    ACS_FLAG_TIMING = 2,   /* time each device launch with CUDA events */
+    ACS_FLAG_TRACE = 4     /* record per-task timestamps (window mode, see acs_get_trace) */
 };
 
 typedef struct acs_config {
@@ -147,7 +148,12 @@ typedef struct acs_config {
     void *cuda_stream;      /* cudaStream_t for all device work (NULL -> a
                                non-blocking stream owned by the context) */
     int32_t device;         /* CUDA device ordinal (-1 -> current) */
-    uint32_t reserved[7];   /* must be 0 */
+    uint32_t poll_ns;       /* longest sleep of an idle worker between polls of
+                               the work ring (0 -> 128 ns; a tuning knob) */
+    uint32_t ctas_per_sm;   /* cap on co-resident persistent CTAs per SM, enforced
+                               through their shared-memory reservation (0 -> as
+                               many as registers allow; a tuning knob) */
+    uint32_t reserved[5];   /* must be 0 */
 } acs_config;
 
 typedef struct acs_stats {
@@ -163,6 +169,10 @@ typedef struct acs_stats {
     uint64_t sched_cycles;      /* window mode: SM clock cycles the scheduler warps ran */
     uint64_t sched_busy_cycles; /* ... of which spent inserting, retiring, dispatching */
     uint64_t sched_inserts;     /* tasks inserted into windows */
+    uint64_t sched_iterations;  /* scheduler loop iterations */
+    uint64_t sched_phase_cycles[8]; /* scheduler-loop cycles by phase: descriptor loads,
+                                   inserts, retire, dispatch selection, ring-cell checks,
+                                   cell aux words, publication fence, cell stores */
     uint32_t cta_slots;         /* worker CTAs of the persistent kernel */
     uint32_t grid;              /* total CTAs of the persistent kernel */
 } acs_stats;
@@ -253,6 +263,15 @@ int acs_sync(acs_ctx *ctx);
  */
 int acs_get_log(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n,
                 uint64_t *masks, uint64_t *start, uint64_t *retire);
+
+/*
+ * Copy the window-mode timestamps (device %globaltimer, ns) of tasks [first,
+ * first + n) of `stream` into t[5*n]: for task i, t[5i+0] insertion into the
+ * window, t[5i+1] dispatch, t[5i+2] start of its first CTA, t[5i+3] end of its
+ * last CTA, t[5i+4] retirement seen by the scheduler. Needs ACS_FLAG_TRACE and
+ * a completed acs_sync; same range rules as acs_get_log. Errors: ACS_ERR_INVALID.
+ */
+int acs_get_trace(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n, uint64_t *t);
 
 /* Copy the context's counters into *out (after acs_sync for device figures). */
 int acs_get_stats(acs_ctx *ctx, acs_stats *out);

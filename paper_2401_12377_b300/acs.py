@@ -35,7 +35,7 @@ OPS = {"nop": 0, "axpy": 1, "scale": 2, "add": 3, "gemv": 4, "bias_relu": 5, "re
        "rl_broadphase": 10, "rl_solve": 11, "rl_integrate": 12, "wait_flag": 30, "sleep": 31}
 
 ACS_MODE_WINDOW, ACS_MODE_INORDER, ACS_MODE_GRAPH = 0, 1, 2
-ACS_FLAG_LOG, ACS_FLAG_TIMING = 1, 2
+ACS_FLAG_LOG, ACS_FLAG_TIMING, ACS_FLAG_TRACE = 1, 2, 4
 
 ACS_RL_SPHERES = 32
 ACS_RL_REC_BYTES = 1088
@@ -54,7 +54,7 @@ class acs_config(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("n_streams", C.c_uint32), ("cta_slots", C.c_uint32),
                 ("capacity", C.c_uint32), ("log_capacity", C.c_uint32), ("flags", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-                ("reserved", C.c_uint32 * 7)]
+                ("poll_ns", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
 
 class acs_stats(C.Structure):
@@ -62,7 +62,9 @@ class acs_stats(C.Structure):
                 ("seg_bytes", C.c_uint64), ("kernel_ms", C.c_double), ("graph_build_ms", C.c_double),
                 ("graph_instantiate_ms", C.c_double), ("graph_edges", C.c_uint64),
                 ("sched_cycles", C.c_uint64), ("sched_busy_cycles", C.c_uint64),
-                ("sched_inserts", C.c_uint64), ("cta_slots", C.c_uint32), ("grid", C.c_uint32)]
+                ("sched_inserts", C.c_uint64), ("sched_iterations", C.c_uint64),
+                ("sched_phase_cycles", C.c_uint64 * 8), ("cta_slots", C.c_uint32),
+                ("grid", C.c_uint32)]
 
 
 # numpy image of acs_args (64 bytes) for packing many tasks at once
@@ -70,7 +72,7 @@ ARGS_DTYPE = np.dtype([("op", "<u2"), ("ncta", "<u2"), ("reserved", "<u4"), ("by
 assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
-           "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_stats", "acs_graph_replay",
+           "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_get_stats", "acs_graph_replay",
            "acs_error", "acs_strerror", "acs_destroy"]
 
 _lib = None
@@ -98,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.acs_sync.argtypes = [C.c_void_p]
     lib.acs_get_log.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
                                 C.c_void_p]
+    lib.acs_get_trace.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p]
     lib.acs_get_stats.argtypes = [C.c_void_p, P(acs_stats)]
     lib.acs_graph_replay.argtypes = [C.c_void_p]
     lib.acs_error.argtypes = [C.c_void_p]
@@ -190,6 +193,13 @@ def acs_get_log(ctx, stream: int, first: int, n: int):
     return masks, start, retire
 
 
+def acs_get_trace(ctx, stream: int, first: int, n: int) -> np.ndarray:
+    """(n, 5) globaltimer ns: insert, dispatch, first-CTA start, last-CTA end, retire seen."""
+    t = np.zeros((n, 5), np.uint64)
+    check(load().acs_get_trace(ctx, stream, first, n, t.ctypes.data), "acs_get_trace")
+    return t
+
+
 def acs_get_stats(ctx) -> acs_stats:
     s = acs_stats()
     check(load().acs_get_stats(ctx, C.byref(s)), "acs_get_stats")
@@ -213,4 +223,6 @@ def acs_destroy(ctx) -> None:
 
 
 def stats_dict(s: acs_stats) -> dict:
-    return {k: getattr(s, k) for k, _ in acs_stats._fields_}
+    out = {k: getattr(s, k) for k, _ in acs_stats._fields_}
+    out["sched_phase_cycles"] = list(s.sched_phase_cycles)
+    return out

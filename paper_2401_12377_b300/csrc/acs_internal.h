@@ -12,7 +12,6 @@ constexpr int kBlock = ACS_BLOCK_THREADS;
 constexpr int kMaxSegs = ACS_MAX_SEGS;
 constexpr int kMaxWindow = ACS_MAX_WINDOW;
 constexpr int kPrefetch = 16;          // descriptors per prefetch batch (bulk copy)
-constexpr int kRowSegs = kMaxSegs + 1; // window row stride in segments (1 pad: bank spread)
 constexpr int kBodySmem = 4096;        // shared memory reserved for task bodies
 constexpr uint32_t kMinCapacity = 64;
 
@@ -75,21 +74,41 @@ struct HostStatus {
 };
 
 // Per-stream scheduler statistics (device), accumulated over launches.
+// scheduler-loop phases timed with clock64: 0 descriptor loads, 1 inserts,
+// 2 retire (incl. waiting for the done polls), 3 dispatch selection,
+// 4 ring-cell checks, 5 aux words, 6 publication fence, 7 cell stores
+constexpr int kPhases = 8;
+
 struct SchedStats {
     unsigned long long cycles;
     unsigned long long busy_cycles;
     unsigned long long inserts;
-    unsigned long long pad;
+    unsigned long long iterations;
+    unsigned long long phase[kPhases];
+};
+
+// per-task trace fields (globaltimer ns): insert, dispatch, first CTA start,
+// last CTA end, retirement seen by the scheduler
+constexpr int kTraceFields = 5;
+
+// Second word of a work-ring cell: the upstream slots the unit's worker must
+// still wait for (bit b: the task in window slot b) and the task's seq.
+struct alignas(16) CellAux {
+    unsigned long long up;
+    uint32_t seq;
+    uint32_t pad;
 };
 
 struct KParams {
     TaskRec *recs;            // [n_streams][capacity]
     DevCtl *ctl;
     unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
+    CellAux *cellaux;         // [cells]
     uint32_t *done;           // [n_streams][kMaxWindow]: seq + 1 of the slot's retired task
     uint32_t *remaining;      // [n_streams][kMaxWindow]: CTAs of the slot's task that finished
     unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
     SchedStats *sched_stats;  // [n_streams]
+    unsigned long long *trace;  // [n_streams][log_capacity][kTraceFields] (ACS_FLAG_TRACE)
     HostStatus *hstatus;      // mapped host memory
     unsigned long long timeout_ns;
     uint32_t cap_log2;        // capacity = 1 << cap_log2
@@ -99,18 +118,18 @@ struct KParams {
     uint32_t n_streams;       // = scheduler CTAs (CTA s < n_streams schedules stream s)
     uint32_t flags;
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses
-    uint32_t pad;
+    uint32_t poll_ns;         // longest sleep of an idle worker between ring polls
     uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
     uint32_t end[ACS_MAX_STREAMS];    // one past the last seq of this launch
 };
 
+// descriptors kept in a scheduler's shared-memory history ring: the W - 1
+// predecessors of every task being checked plus look-ahead
+__host__ __device__ inline uint32_t hist_size(uint32_t window) { return window <= 32 ? 64u : 128u; }
+
 inline uint32_t sched_smem_bytes(uint32_t window) {
-    uint32_t rows = window * kRowSegs * (uint32_t)sizeof(Seg);
-    uint32_t meta = window * 4;                       // wmask (u16) + nseg (u8) + pad
-    uint32_t pf = 2 * kPrefetch * (uint32_t)sizeof(TaskRec);
-    uint32_t total = rows + meta;
-    total = (total + 127) & ~127u;
-    return total + pf + 64;                           // + two mbarriers
+    const uint32_t H = hist_size(window);
+    return H * (uint32_t)sizeof(TaskRec) + H * 8 + H * 4 + (H / kPrefetch) * 8 + 16 + 32 * 24;
 }
 
 inline uint32_t dyn_smem_bytes(uint32_t window) {

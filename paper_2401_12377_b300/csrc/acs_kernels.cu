@@ -35,6 +35,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -79,6 +84,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void raise_error(const KParams &P, uint32_t code, uint32_t site) {
     if (atomicCAS(&P.ctl->err, 0u, code) == 0u) P.ctl->err_info = site;
     __threadfence();
@@ -87,42 +110,158 @@ __device__ __forceinline__ void raise_error(const KParams &P, uint32_t code, uin
 
 __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u32(&P.ctl->stop) != 0; }
 
-// ---- scheduler warp -------------------------------------------------------------
+// ---- scheduler CTA ----------------------------------------------------------------
+//
+// Shared memory of a scheduler CTA (stream s):
+//   hist[H]     the descriptors of tasks seq mod H, streamed in by bulk copy in
+//               batches of kPrefetch aligned to kPrefetch; it holds the W - 1
+//               predecessors of every task still to be checked
+//   pmask[H]    upstream-candidate mask of task seq mod H (bit i mod W for
+//               each conflicting predecessor i in [seq - W + 1, seq - 1])
+//   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
+//   bar[H/16]   one mbarrier per batch position of hist
+//   sh          counters shared by the warps
+//
+// Warps 1..7 ("checkers") compute pmask for tasks j = first + w - 1 + 7k: the
+// segment-overlap test of Alg. 1 (extended to RAW) of task j against its W - 1
+// predecessors, one predecessor per lane, ballot -> mask. The candidate set of
+// a task is fixed by the stream, so the test runs ahead of execution, in
+// parallel with it. Warp 0 owns the state machine: it loads descriptors,
+// inserts checked tasks into the W-slot ring (upstream = pmask & active slots),
+// polls completion, releases slots in program order and dispatches.
+
+struct SchedShared {
+    uint32_t complete_upto;  // hist holds every seq below (loaded), from `lo`
+    uint32_t next;           // tasks below are inserted
+    uint32_t quit;           // 1: checkers leave
+    uint32_t pad;
+};
+
+struct DispatchEntry {
+    unsigned long long up;   // upstream slots the workers must still wait for
+    uint32_t n;              // ncta
+    uint32_t seq;
+    uint32_t end;            // inclusive prefix of n over ranks
+    uint32_t pad;
+};
 
 struct SchedSmem {
-    Seg *rows;        // [W][kRowSegs]
-    uint16_t *wmask;  // [W]
-    uint8_t *nseg;    // [W]
-    TaskRec *pf;      // [2][kPrefetch]
-    uint64_t *bar;    // [2]
+    DispatchEntry *disp;     // [32] tasks of the current dispatch batch, by age
+    TaskRec *hist;
+    unsigned long long *pmask;
+    uint32_t *ptag;
+    uint64_t *bar;
+    SchedShared *sh;
+    uint32_t H;
 };
 
 __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     SchedSmem s;
-    s.rows = reinterpret_cast<Seg *>(smem);
-    s.wmask = reinterpret_cast<uint16_t *>(smem + W * kRowSegs * sizeof(Seg));
-    s.nseg = reinterpret_cast<uint8_t *>(s.wmask + W);
-    uint32_t off = W * kRowSegs * (uint32_t)sizeof(Seg) + W * 4;
-    off = (off + 127) & ~127u;
-    s.pf = reinterpret_cast<TaskRec *>(smem + off);
-    s.bar = reinterpret_cast<uint64_t *>(smem + off + 2 * kPrefetch * sizeof(TaskRec));
+    s.H = hist_size(W);
+    uint8_t *p = smem;
+    s.hist = reinterpret_cast<TaskRec *>(p);
+    p += s.H * sizeof(TaskRec);
+    s.pmask = reinterpret_cast<unsigned long long *>(p);
+    p += s.H * sizeof(unsigned long long);
+    s.ptag = reinterpret_cast<uint32_t *>(p);
+    p += s.H * sizeof(uint32_t);
+    s.bar = reinterpret_cast<uint64_t *>(p);
+    p += (s.H / kPrefetch) * sizeof(uint64_t);
+    s.sh = reinterpret_cast<SchedShared *>(p);
+    p += sizeof(SchedShared);
+    s.disp = reinterpret_cast<DispatchEntry *>(p);
     return s;
 }
 
-// Does a task with segments (a, an, aw) conflict with the task held in window
-// row `row` (rn segments, write mask rw)? Alg. 1's overlap test on inclusive
-// ranges; a pair counts unless both segments are reads.
-__device__ __forceinline__ bool row_conflict(const Seg *a, int an, uint32_t aw, const Seg *row, int rn,
-                                             uint32_t rw) {
-    for (int x = 0; x < an; ++x) {
-        const Seg sa = a[x];
-        const bool xa = (aw >> x) & 1u;
-        for (int y = 0; y < rn; ++y) {
-            const Seg sb = row[y];
-            if ((xa || ((rw >> y) & 1u)) && sa.start <= sb.last && sb.start <= sa.last) return true;
+__device__ __forceinline__ uint32_t lds_volatile(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+__device__ __forceinline__ void sts_volatile(uint32_t *p, uint32_t v) { *(volatile uint32_t *)p = v; }
+
+// Alg. 1's overlap test between task i (earlier) and task j on inclusive
+// ranges; a segment pair counts unless both are reads (RAW, WAR, WAW).
+__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const TaskRec &rj) {
+    const int ni = ri.nseg, nj = rj.nseg;
+    const uint32_t wi = ri.wmask, wj = rj.wmask;
+    for (int y = 0; y < ni; ++y) {
+        const Seg b = ri.seg[y];
+        const bool yw = (wi >> y) & 1u;
+        for (int x = 0; x < nj; ++x) {
+            const Seg a = rj.seg[x];
+            if ((yw || ((wj >> x) & 1u)) && a.start <= b.last && b.start <= a.last) return true;
         }
     }
     return false;
+}
+
+__device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw, uint32_t w) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t W = P.window;
+    const uint32_t first = P.first[stream], end = P.end[stream];
+    SchedSmem S = carve(smem_raw, W);
+    const uint32_t H = S.H, HM = H - 1;   // H is a power of two
+    constexpr uint32_t kCheckers = kBlock / 32 - 1;
+    unsigned long long tw = 0;
+    for (uint32_t j = first + w; j < end; j += kCheckers) {
+        // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
+        uint32_t spins = 0, backoff = 32;
+        while (true) {
+            const uint32_t cu = lds_volatile(&S.sh->complete_upto);
+            const uint32_t nx = lds_volatile(&S.sh->next);
+            if (cu > j && j < nx + H) break;
+            if (lds_volatile(&S.sh->quit)) return;
+            if ((++spins & 63) == 0) {
+                const unsigned long long now = globaltimer_ns();
+                if (tw == 0) tw = now;
+                else if (now - tw > 4ull * P.timeout_ns) {
+                    if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteSched);
+                    return;
+                }
+            }
+            __nanosleep(backoff);
+            if (backoff < 256) backoff <<= 1;
+        }
+        tw = 0;
+        __threadfence_block();
+        const TaskRec &rj = S.hist[j & HM];
+        bool c0 = false, c1 = false;
+        const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
+        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM], rj);
+        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM], rj);
+        const uint32_t b0 = __ballot_sync(0xffffffffu, c0);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, c1);
+        if (lane == 0) {
+            // candidate at distance d sits in slot (j - d) mod W
+            const uint32_t js = j % W;
+            unsigned long long m = 0;
+            for (uint32_t bits = b0; bits; bits &= bits - 1) {
+                const uint32_t d = (uint32_t)__ffs(bits);          // 1 .. 32
+                m |= 1ull << (js >= d ? js - d : js + W - d);
+            }
+            for (uint32_t bits = b1; bits; bits &= bits - 1) {
+                const uint32_t d = (uint32_t)__ffs(bits) + 32u;    // 33 .. 63
+                m |= 1ull << (js >= d ? js - d : js + W - d);
+            }
+            S.pmask[j & HM] = m;
+            __threadfence_block();
+            sts_volatile(&S.ptag[j & HM], j + 1u);
+        }
+        __syncwarp();
+    }
+}
+
+// Shared-memory set-up of a scheduler CTA, before its warps take their roles
+// (followed by __syncthreads in the caller).
+__device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
+    const uint32_t W = P.window;
+    const uint32_t first = P.first[stream];
+    SchedSmem S = carve(smem_raw, W);
+    for (uint32_t i = threadIdx.x; i < S.H; i += blockDim.x) S.ptag[i] = 0;
+    if (threadIdx.x < S.H / kPrefetch) mbar_init(&S.bar[threadIdx.x], 1);
+    if (threadIdx.x == 0) {
+        S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
+        S.sh->next = first;
+        S.sh->quit = 0;
+        fence_mbar_init();
+    }
 }
 
 __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
@@ -133,231 +272,355 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const TaskRec *recs = P.recs + (size_t)stream * C;
     uint32_t *done = P.done + stream * kMaxWindow;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
+    const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const uint32_t LM = (1u << P.log_log2) - 1u;
-    unsigned long long *lmask = P.log_mask + ((size_t)stream << P.log_log2);
-    unsigned long long *lstart = P.log_start + ((size_t)stream << P.log_log2);
-    unsigned long long *lretire = P.log_retire + ((size_t)stream << P.log_log2);
+    const size_t lbase = (size_t)stream << P.log_log2;
     SchedSmem S = carve(smem_raw, W);
+    const uint32_t H = S.H, HM = H - 1, NB = H / kPrefetch;
     const unsigned long long t_begin = clock64();
     unsigned long long busy = 0, inserts = 0;
-    if (first >= end) goto finish;
 
-    {
-        // per-lane slot registers: slot lane (index 0) and lane + 32 (index 1)
-        uint32_t st[2] = {kEmpty, kEmpty}, sq[2] = {0, 0}, nc[2] = {0, 0};
-        unsigned long long mk[2] = {0, 0};
+    // per-lane slot registers: slot lane (index 0) and lane + 32 (index 1)
+    uint32_t st0 = kEmpty, st1 = kEmpty, sq0 = 0, sq1 = 0, nc0 = 0, nc1 = 0;
+    unsigned long long mk0 = 0, mk1 = 0;
 
-        // Reload the W - 1 tasks before `first` (retired in earlier launches):
-        // they stay upstream candidates for the log of the first inserts.
-        const uint32_t lo = first > W - 1 ? first - (W - 1) : 0u;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t slot = lane + 32u * h;
-            if (slot < W && first > lo) {
-                const uint32_t s = first - 1 - ((first - 1 - slot + W * 64u) % W);  // s = slot mod W
-                if (s >= lo && s < first) {
-                    const TaskRec *r = recs + (s & (C - 1));
-                    const uint32_t n = r->nseg;
-                    for (uint32_t k = 0; k < n; ++k) S.rows[slot * kRowSegs + k] = r->seg[k];
-                    S.nseg[slot] = (uint8_t)n;
-                    S.wmask[slot] = r->wmask;
-                    st[h] = kRetired;
-                    sq[h] = s;
-                }
-            }
-        }
-        if (lane == 0) {
-            mbar_init(&S.bar[0], 1);
-            mbar_init(&S.bar[1], 1);
-            fence_mbar_init();
-        }
-        __syncwarp();
+    const uint32_t lo = first > W - 1 ? first - (W - 1) : 0u;   // oldest record loaded
 
-        // prefetch bookkeeping (uniform across lanes)
-        uint32_t pf_batch[2] = {0xffffffffu, 0xffffffffu};
-        uint32_t pf_phase[2] = {0, 0};
-        bool pf_busy[2] = {false, false};
-        uint32_t issued = 0xffffffffu;  // highest batch issued
-        auto issue = [&](uint32_t m) {
-            const uint32_t b = m & 1u;
-            const uint32_t blo = max(m * kPrefetch, first);
-            const uint32_t bhi = min(m * kPrefetch + kPrefetch, end);
-            pf_batch[b] = m;
-            issued = m;
-            if (blo >= bhi) return;
-            if (lane == 0) {
-                const uint32_t bytes = (bhi - blo) * (uint32_t)sizeof(TaskRec);
-                fence_proxy_async();
-                mbar_expect_tx(&S.bar[b], bytes);
-                bulk_g2s(&S.pf[b * kPrefetch + (blo - m * kPrefetch)], recs + (blo & (C - 1)), bytes, &S.bar[b]);
-            }
-            pf_busy[b] = true;
-        };
-        issue(first / kPrefetch);
-        if ((first / kPrefetch + 1) * kPrefetch < end) issue(first / kPrefetch + 1);
-
-        uint32_t head = first, next = first;
-        unsigned long long idle_since = 0;  // 0: made progress in the last iteration
-        uint32_t iter = 0;
-        while (true) {
-            bool progress = false;
-            const unsigned long long t0 = clock64();
-
-            // 1. retire: poll the done word of every executing slot
-            bool ret[2] = {false, false};
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (st[h] == kExec) ret[h] = ld_acquire_u32(&done[lane + 32u * h]) == sq[h] + 1u;
-            unsigned long long R = __ballot_sync(0xffffffffu, ret[0]);
-            if (W > 32) R |= (unsigned long long)__ballot_sync(0xffffffffu, ret[1]) << 32;
-            if (R) {
-                progress = true;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    mk[h] &= ~R;
-                    if (ret[h]) st[h] = kRetired;
-                    if (st[h] == kPending && mk[h] == 0) st[h] = kReady;
-                }
-                // 2. release retired slots in program order
-                while (head < next) {
-                    const uint32_t s = head % W;
-                    const uint32_t v = __shfl_sync(0xffffffffu, s < 32 ? st[0] : st[1], s & 31);
-                    if (v != kRetired) break;
-                    ++head;
-                }
-            }
-            if (head == end) { busy += clock64() - t0; break; }
-
-            // 3. insert while a slot is free and the descriptor is at hand
-            while (next < end && next - head < W) {
-                const uint32_t m = next / kPrefetch, b = m & 1u;
-                if (pf_batch[b] != m) break;  // not issued yet (issued below)
-                if (pf_busy[b]) {
-                    if (!mbar_try_wait(&S.bar[b], pf_phase[b])) break;
-                    pf_phase[b] ^= 1u;
-                    pf_busy[b] = false;
-                }
-                if (issued == m && (m + 1) * kPrefetch < end) issue(m + 1);
-                const TaskRec *r = &S.pf[b * kPrefetch + (next - m * kPrefetch)];
-                const uint32_t an = r->nseg, aw = r->wmask;
-                const uint32_t js = next % W;
-                bool c[2] = {false, false};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t slot = lane + 32u * h;
-                    if (slot < W && slot != js && st[h] != kEmpty)
-                        c[h] = row_conflict(r->seg, an, aw, &S.rows[slot * kRowSegs], S.nseg[slot], S.wmask[slot]);
-                }
-                unsigned long long pre = __ballot_sync(0xffffffffu, c[0]);
-                if (W > 32) pre |= (unsigned long long)__ballot_sync(0xffffffffu, c[1]) << 32;
-                const bool a0 = st[0] == kPending || st[0] == kReady || st[0] == kExec;
-                const bool a1 = st[1] == kPending || st[1] == kReady || st[1] == kExec;
-                unsigned long long act = __ballot_sync(0xffffffffu, a0);
-                if (W > 32) act |= (unsigned long long)__ballot_sync(0xffffffffu, a1) << 32;
-                const unsigned long long up = pre & act;
-                if (lane < an) S.rows[js * kRowSegs + lane] = r->seg[lane];
-                if (lane == 0) {
-                    S.nseg[js] = (uint8_t)an;
-                    S.wmask[js] = (uint16_t)aw;
-                    if (logging) {
-                        lmask[next & LM] = pre;
-                        lstart[next & LM] = ~0ull;
-                        lretire[next & LM] = 0ull;
-                    }
-                }
-                if ((js & 31) == lane) {
-                    if (js < 32) { st[0] = up ? kPending : kReady; mk[0] = up; sq[0] = next; nc[0] = r->ncta; }
-                    else         { st[1] = up ? kPending : kReady; mk[1] = up; sq[1] = next; nc[1] = r->ncta; }
-                }
-                __syncwarp();
-                ++next;
-                ++inserts;
-                progress = true;
-            }
-
-            // 4. dispatch ready tasks, oldest first
-            unsigned long long RD = __ballot_sync(0xffffffffu, st[0] == kReady);
-            if (W > 32) RD |= (unsigned long long)__ballot_sync(0xffffffffu, st[1] == kReady) << 32;
-            if (RD) {
-                progress = true;
-                const uint32_t hs = head % W;
-                const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
-                const unsigned long long rot = ((RD >> hs) | (RD << ((W - hs) % W))) & full;
-                unsigned long long rr = rot;
-                while (rr) {
-                    const uint32_t bit = __ffsll((long long)rr) - 1;
-                    rr &= rr - 1;
-                    const uint32_t s = (bit + hs) % W;
-                    const uint32_t n = __shfl_sync(0xffffffffu, s < 32 ? nc[0] : nc[1], s & 31);
-                    const uint32_t q = __shfl_sync(0xffffffffu, s < 32 ? sq[0] : sq[1], s & 31);
-                    uint32_t p0 = 0;
-                    if (lane == 0) p0 = atomicAdd(&P.ctl->ring_tail, n);
-                    p0 = __shfl_sync(0xffffffffu, p0, 0);
-                    const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
-                    for (uint32_t cta = lane; cta < n; cta += 32) {
-                        const uint32_t pos = p0 + cta;
-                        unsigned long long *cell = &P.cells[pos & P.cell_mask];
-                        // the cell is free for position pos once its sequence reads pos
-                        unsigned long long tw = 0;
-                        uint32_t spins = 0;
-                        bool ok = true;
-                        while ((uint32_t)ld_acquire_u64(cell) != pos) {
-                            if ((++spins & 63) == 0) {
-                                const unsigned long long now = globaltimer_ns();
-                                if (tw == 0) tw = now;
-                                else if (now - tw > P.timeout_ns) {
-                                    raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
-                                    ok = false;
-                                    break;
-                                }
-                                if (stopped(P)) { ok = false; break; }
-                            }
-                        }
-                        const unsigned long long payload = ((unsigned long long)gidx << 8) | cta;
-                        if (ok) st_release_u64(cell, (payload << 32) | (unsigned long long)(pos + 1u));
-                    }
-                    if ((s & 31) == lane) {
-                        if (s < 32) st[0] = kExec;
-                        else st[1] = kExec;
-                    }
-                    __syncwarp();
-                }
-            }
-
-            if (progress) {
-                busy += clock64() - t0;
-                idle_since = 0;
-            } else {
-                const unsigned long long now = globaltimer_ns();
-                if (idle_since == 0) idle_since = now;
-                else if (now - idle_since > P.timeout_ns) {
-                    if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteSched);
-                    break;
-                }
-            }
-            if (((++iter & 31) == 0 || !progress) && stopped(P)) break;
-        }
-        // drain a bulk copy still in flight before the CTA may exit
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            if (pf_busy[b]) {
-                const unsigned long long tw = globaltimer_ns();
-                while (!mbar_try_wait(&S.bar[b], pf_phase[b])) {
-                    if (globaltimer_ns() - tw > P.timeout_ns) {
-                        if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSitePrefetch);
-                        break;
-                    }
-                }
-            }
-        }
+    uint32_t load_upto = lo, complete_upto = lo, bph = 0;  // bph: parity bit per barrier
+    uint32_t head = first, next = first;
+    uint32_t hslot = first % W, nslot = first % W;   // head % W, next % W
+    const bool sole_producer = P.n_streams == 1;
+    uint32_t tail = sole_producer ? ld_volatile_u32(&P.ctl->ring_tail) : 0u;
+    unsigned long long pre_cell0 = 0, pre_cell1 = 0;   // cells tail + lane, tail + 32 + lane
+    if (sole_producer) {
+        pre_cell0 = ld_relaxed_u64(&P.cells[(tail + lane) & P.cell_mask]);
+        pre_cell1 = ld_relaxed_u64(&P.cells[(tail + 32 + lane) & P.cell_mask]);
     }
+    unsigned long long idle_since = 0;
+    uint32_t iter = 0;
+    bool failed = false;
+    unsigned long long ph[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long tp = 0;
+#define ACS_PHASE(k) do { const unsigned long long _t = clock64(); ph[k] += _t - tp; tp = _t; } while (0)
 
-finish:
+    while (first < end) {
+        bool progress = false;
+        const unsigned long long t0 = clock64();
+        tp = t0;
+
+        // 0. stream descriptors into hist (never over a record still needed)
+        while (load_upto < end) {
+            // hist[s mod H] may take seq s once s - H is neither a candidate
+            // of an unchecked task nor uninserted: s < next + H - W + 1
+            const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
+            if (bhi + W > next + H + 1) break;
+            if (lane == 0) {
+                const uint32_t bytes = (bhi - load_upto) * (uint32_t)sizeof(TaskRec);
+                uint64_t *bar = &S.bar[(load_upto / kPrefetch) % NB];
+                fence_proxy_async();
+                mbar_expect_tx(bar, bytes);
+                bulk_g2s(&S.hist[load_upto & HM], recs + (load_upto & (C - 1)), bytes, bar);
+            }
+            load_upto = bhi;
+        }
+        while (complete_upto < load_upto) {
+            const uint32_t x = (complete_upto / kPrefetch) % NB;
+            if (!mbar_test_wait(&S.bar[x], (bph >> x) & 1u)) break;
+            bph ^= 1u << x;
+            complete_upto = min((complete_upto / kPrefetch + 1) * kPrefetch, end);
+            __threadfence_block();
+            if (lane == 0) sts_volatile(&S.sh->complete_upto, complete_upto);
+        }
+
+        ACS_PHASE(0);
+        // 1. how many tasks are checked and have a free slot (at most 32 per
+        //    iteration); one CTA-scope fence orders the tag reads before the
+        //    mask reads (before the global polls below, so it never waits on them)
+        uint32_t nins = 0;
+        {
+            const uint32_t cap = min(min(end - next, W - (next - head)), 32u);
+            const bool ok = lane < cap && lds_volatile(&S.ptag[(next + lane) & HM]) == next + lane + 1u;
+            const uint32_t okm = __ballot_sync(0xffffffffu, ok);
+            nins = __ffs(~okm) - 1;          // leading run of checked tasks
+            if (okm == 0xffffffffu) nins = 32;
+        }
+        if (nins) __threadfence_block();
+
+        // 2. issue the done-word loads of executing slots; their latency
+        //    overlaps the inserts
+        uint32_t dv0 = 0, dv1 = 0;
+        if (st0 == kExec) dv0 = ld_relaxed_u32(&done[lane]);
+        if (st1 == kExec) dv1 = ld_relaxed_u32(&done[lane + 32u]);
+
+        const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
+        // 3. insert, lane k taking task next + k: upstream = its candidates
+        //    still active, the new tasks before it included
+        if (nins) {
+            unsigned long long act = __ballot_sync(0xffffffffu, st0 == kPending || st0 == kReady || st0 == kExec);
+            if (W > 32)
+                act |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kPending || st1 == kReady || st1 == kExec) << 32;
+            const bool mine = lane < nins;
+            const uint32_t q = next + lane;
+            const unsigned long long pre = mine ? S.pmask[q & HM] : 0ull;
+            const uint32_t ncta = mine ? S.hist[q & HM].ncta : 0u;
+            // slots nslot .. nslot + lane - 1 (mod W) hold the earlier new tasks
+            const unsigned long long low = (1ull << lane) - 1ull;
+            const unsigned long long newer = nslot ? (((low << nslot) | (low >> (W - nslot))) & full) : low;
+            const unsigned long long up = pre & (act | newer);
+            if (mine && (logging || tracing)) {
+                const size_t li = lbase + (q & LM);
+                if (logging) {
+                    P.log_mask[li] = pre;
+                    P.log_start[li] = ~0ull;
+                    P.log_retire[li] = 0ull;
+                }
+                if (tracing) {
+                    P.trace[li * kTraceFields + 0] = globaltimer_ns();
+                    P.trace[li * kTraceFields + 2] = ~0ull;   // first-CTA start: atomicMin target
+                }
+            }
+            // hand each task to the lane owning its slot
+            const uint32_t k0 = lane >= nslot ? lane - nslot : lane + W - nslot;
+            const uint32_t u0l = __shfl_sync(0xffffffffu, (uint32_t)up, k0 & 31);
+            const uint32_t u0h = __shfl_sync(0xffffffffu, (uint32_t)(up >> 32), k0 & 31);
+            const uint32_t n0 = __shfl_sync(0xffffffffu, ncta, k0 & 31);
+            if (lane < W && k0 < nins) {
+                mk0 = (unsigned long long)u0l | ((unsigned long long)u0h << 32);
+                st0 = mk0 ? kPending : kReady;
+                sq0 = next + k0;
+                nc0 = n0;
+            }
+            if (W > 32) {
+                const uint32_t s1 = lane + 32u;
+                const uint32_t k1 = s1 >= nslot ? s1 - nslot : s1 + W - nslot;
+                const uint32_t u1l = __shfl_sync(0xffffffffu, (uint32_t)up, k1 & 31);
+                const uint32_t u1h = __shfl_sync(0xffffffffu, (uint32_t)(up >> 32), k1 & 31);
+                const uint32_t n1 = __shfl_sync(0xffffffffu, ncta, k1 & 31);
+                if (s1 < W && k1 < nins) {
+                    mk1 = (unsigned long long)u1l | ((unsigned long long)u1h << 32);
+                    st1 = mk1 ? kPending : kReady;
+                    sq1 = next + k1;
+                    nc1 = n1;
+                }
+            }
+            next += nins;
+            nslot += nins;
+            if (nslot >= W) nslot -= W;
+            inserts += nins;
+            progress = true;
+            if (lane == 0) sts_volatile(&S.sh->next, next);
+        }
+        ACS_PHASE(1);
+
+        // 4. retire: a slot retires when its done word reads seq + 1
+        const bool ret0 = st0 == kExec && dv0 == sq0 + 1u;
+        const bool ret1 = st1 == kExec && dv1 == sq1 + 1u;
+        unsigned long long R = __ballot_sync(0xffffffffu, ret0);
+        if (W > 32) R |= (unsigned long long)__ballot_sync(0xffffffffu, ret1) << 32;
+        if (R) {
+            progress = true;
+            mk0 &= ~R;
+            mk1 &= ~R;
+            if (ret0) st0 = kRetired;
+            if (ret1) st1 = kRetired;
+            if (st0 == kPending && mk0 == 0) st0 = kReady;
+            if (st1 == kPending && mk1 == 0) st1 = kReady;
+            if (tracing) {
+                const unsigned long long now = globaltimer_ns();
+                if (ret0) P.trace[(lbase + (sq0 & LM)) * kTraceFields + 4] = now;
+                if (ret1) P.trace[(lbase + (sq1 & LM)) * kTraceFields + 4] = now;
+            }
+            // release in program order: the run of retired slots from the head
+            unsigned long long RT = __ballot_sync(0xffffffffu, st0 == kRetired);
+            if (W > 32) RT |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kRetired) << 32;
+            const unsigned long long rrt = hslot ? (((RT >> hslot) | (RT << (W - hslot))) & full) : RT;
+            uint32_t run = rrt == ~0ull ? 64u : (uint32_t)(__ffsll((long long)~rrt) - 1);
+            run = min(run, next - head);
+            head += run;
+            hslot += run;
+            if (hslot >= W) hslot -= W;
+        }
+        ACS_PHASE(2);
+        if (head == end) { busy += clock64() - t0; break; }
+
+        // 5. dispatch, oldest first, at most 32 undispatched tasks whose active
+        //    upstream tasks are all dispatched (or in this batch). A task still
+        //    pending carries its upstream mask in the cell; its worker CTAs
+        //    wait on those done words themselves, so no retire -> dispatch
+        //    relay through this warp sits on a dependency chain. Units enter
+        //    the FIFO ring after their upstream tasks' units, which keeps the
+        //    waits deadlock-free: the oldest unfinished unit never waits.
+        const bool nd0 = st0 == kPending || st0 == kReady;
+        const bool nd1 = st1 == kPending || st1 == kReady;
+        unsigned long long undisp = __ballot_sync(0xffffffffu, nd0);
+        if (W > 32) undisp |= (unsigned long long)__ballot_sync(0xffffffffu, nd1) << 32;
+        unsigned long long sel = 0;
+        while (undisp & ~sel) {
+            const unsigned long long waiting = undisp & ~sel;
+            const bool e0 = nd0 && !((sel >> lane) & 1ull) && (mk0 & waiting) == 0;
+            const bool e1 = nd1 && !((sel >> (lane + 32)) & 1ull) && (mk1 & waiting) == 0;
+            unsigned long long nw = __ballot_sync(0xffffffffu, e0);
+            if (W > 32) nw |= (unsigned long long)__ballot_sync(0xffffffffu, e1) << 32;
+            if (!nw) break;
+            sel |= nw;
+        }
+        if (sel) {
+            progress = true;
+            const uint32_t hs = hslot;
+            unsigned long long rot = hs ? (((sel >> hs) | (sel << (W - hs))) & full) : sel;   // bit a: age a
+            while (__popcll(rot) > 32) rot &= ~(1ull << (63 - __clzll((long long)rot)));   // oldest 32
+            // owner lanes post (ncta, seq, upstream) under their age rank
+            DispatchEntry *D = S.disp;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t sl = lane + 32u * h;
+                if (sl < W) {
+                    const uint32_t age = sl >= hs ? sl - hs : sl + W - hs;
+                    if ((rot >> age) & 1ull) {
+                        const uint32_t rank = __popcll(rot & ((1ull << age) - 1ull));
+                        D[rank].n = h ? nc1 : nc0;
+                        D[rank].seq = h ? sq1 : sq0;
+                        D[rank].up = h ? mk1 : mk0;
+                        if (h) st1 = kExec; else st0 = kExec;
+                    }
+                }
+            }
+            __syncwarp();
+            const uint32_t nsel = __popcll(rot);
+            // ring offsets: inclusive prefix of ncta over ranks
+            const uint32_t my_n = lane < nsel ? D[lane].n : 0u;
+            uint32_t incl = my_n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += v;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane < nsel) D[lane].end = incl;
+            __syncwarp();
+            uint32_t p0;
+            if (sole_producer) {
+                p0 = tail;
+            } else {
+                p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&P.ctl->ring_tail, total);
+                p0 = __shfl_sync(0xffffffffu, p0, 0);
+            }
+            tail = p0 + total;
+            ACS_PHASE(3);
+            // a cell is free for position p once its sequence word reads p
+            // (the sole producer looked at the next 64 cells ahead of time)
+            bool ok = true;
+            for (uint32_t u = lane; u < total && ok; u += 32) {
+                if (sole_producer && u < 64 && (uint32_t)(u < 32 ? pre_cell0 : pre_cell1) == p0 + u) continue;
+                unsigned long long *cell = &P.cells[(p0 + u) & P.cell_mask];
+                unsigned long long tw = 0;
+                uint32_t spins = 0;
+                while ((uint32_t)ld_relaxed_u64(cell) != p0 + u) {
+                    if ((++spins & 63) == 0) {
+                        const unsigned long long now = globaltimer_ns();
+                        if (tw == 0) tw = now;
+                        else if (now - tw > P.timeout_ns) {
+                            raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
+                            ok = false;
+                            break;
+                        }
+                        if (stopped(P)) { ok = false; break; }
+                    }
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+            ACS_PHASE(4);
+            // aux words (upstream mask still to wait for, seq), one fence, then
+            // the sequence words that publish the units: a worker acquiring its
+            // cell sees its aux word, and everything this warp acquired (done
+            // words of retired predecessors) happens before.
+            uint32_t urank[2] = {0, 0};
+            for (uint32_t u = lane, it2 = 0; u < total; u += 32, ++it2) {
+                uint32_t lo = 0, hi = nsel - 1;          // first rank with end > u
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (D[mid].end > u) hi = mid; else lo = mid + 1;
+                }
+                if (it2 < 2) urank[it2] = lo;
+                CellAux *ax = &P.cellaux[(p0 + u) & P.cell_mask];
+                ax->up = D[lo].up;
+                ax->seq = D[lo].seq;
+            }
+            ACS_PHASE(5);
+            fence_acq_rel_gpu();   // also turns the relaxed done polls above into acquires
+            __syncwarp();          // ... for every lane's stores below, whichever lane polled
+            ACS_PHASE(6);
+            const unsigned long long tnow = tracing ? globaltimer_ns() : 0ull;
+            for (uint32_t u = lane, it2 = 0; u < total; u += 32, ++it2) {
+                uint32_t r;
+                if (it2 < 2) {
+                    r = urank[it2];
+                } else {
+                    uint32_t lo = 0, hi = nsel - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (D[mid].end > u) hi = mid; else lo = mid + 1;
+                    }
+                    r = lo;
+                }
+                const uint32_t q = D[r].seq;
+                const uint32_t cta = u - (D[r].end - D[r].n);
+                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
+                const unsigned long long payload = ((unsigned long long)gidx << 8) | cta;
+                const uint32_t pos = p0 + u;
+                st_relaxed_u64(&P.cells[pos & P.cell_mask], (payload << 32) | (unsigned long long)(pos + 1u));
+            }
+            if (tracing && lane < nsel) P.trace[(lbase + (D[lane].seq & LM)) * kTraceFields + 1] = tnow;
+            __syncwarp();
+        }
+        ACS_PHASE(7);
+        // look at the next 64 cells for the following batch (sole producer)
+        if (sole_producer) {
+            pre_cell0 = ld_relaxed_u64(&P.cells[(tail + lane) & P.cell_mask]);
+            pre_cell1 = ld_relaxed_u64(&P.cells[(tail + 32 + lane) & P.cell_mask]);
+        }
+
+        if (progress) {
+            busy += clock64() - t0;
+            idle_since = 0;
+        } else {
+            const unsigned long long now = globaltimer_ns();
+            if (idle_since == 0) idle_since = now;
+            else if (now - idle_since > P.timeout_ns) {
+                if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteSched);
+                failed = true;
+                break;
+            }
+        }
+        if (((++iter & 31) == 0 || !progress) && stopped(P)) { failed = true; break; }
+    }
+    (void)failed;
+    if (sole_producer && lane == 0) st_relaxed_u32(&P.ctl->ring_tail, tail);
+    if (lane == 0) sts_volatile(&S.sh->quit, 1u);
+    // drain bulk copies still in flight before the CTA may exit
+    while (complete_upto < load_upto) {
+        const uint32_t x = (complete_upto / kPrefetch) % NB;
+        const unsigned long long tw = globaltimer_ns();
+        bool ok = true;
+        while (!mbar_try_wait(&S.bar[x], (bph >> x) & 1u)) {
+            if (globaltimer_ns() - tw > P.timeout_ns) {
+                if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSitePrefetch);
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) break;
+        bph ^= 1u << x;
+        complete_upto = min((complete_upto / kPrefetch + 1) * kPrefetch, end);
+    }
     if (lane == 0) {
         SchedStats *ss = &P.sched_stats[stream];
         ss->cycles += clock64() - t_begin;
         ss->busy_cycles += busy;
         ss->inserts += inserts;
+        ss->iterations += iter;
+        for (int k = 0; k < kPhases; ++k) ss->phase[k] += ph[k];
         __threadfence();
         if (atomicAdd(&P.ctl->sched_done, 1u) == P.n_streams - 1u) {
             __threadfence();
@@ -371,9 +634,14 @@ finish:
 __device__ void worker_loop(const KParams &P, uint8_t *smem) {
     __shared__ uint32_t s_payload;
     __shared__ uint32_t s_quit;
+    __shared__ unsigned long long s_up;
+    __shared__ uint32_t s_seq;
     __shared__ TaskHdr s_hdr;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
+    const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const uint32_t ncells = P.cell_mask + 1u;
+    const uint32_t W = P.window;
+    const uint32_t lane = threadIdx.x & 31;
     while (true) {
         if (threadIdx.x == 0) {
             const uint32_t pos = atomicAdd(&P.ctl->ring_head, 1u);
@@ -381,8 +649,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             uint32_t quit = 0, spins = 0, backoff = 32;
             unsigned long long tw = 0, v;
             while (true) {
-                v = ld_acquire_u64(cell);
-                if ((uint32_t)v == pos + 1u) break;
+                v = ld_relaxed_u64(cell);
+                if ((uint32_t)v == pos + 1u) { fence_acq_rel_gpu(); break; }
                 if ((++spins & 7) == 0) {
                     if (stopped(P)) { quit = 1; break; }
                     const unsigned long long now = globaltimer_ns();
@@ -394,9 +662,14 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     }
                 }
                 __nanosleep(backoff);
-                if (backoff < 512) backoff <<= 1;
+                if (backoff < P.poll_ns) backoff <<= 1;
             }
-            if (!quit) st_relaxed_u64(cell, (unsigned long long)(pos + ncells));  // free for the next lap
+            if (!quit) {
+                const uint4 ax = __ldcg(reinterpret_cast<const uint4 *>(&P.cellaux[pos & P.cell_mask]));
+                s_up = (unsigned long long)ax.x | ((unsigned long long)ax.y << 32);
+                s_seq = ax.z;
+                st_relaxed_u64(cell, (unsigned long long)(pos + ncells));  // free for the next lap
+            }
             s_payload = (uint32_t)(v >> 32);
             s_quit = quit;
         }
@@ -404,13 +677,43 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         if (s_quit) break;
         const uint32_t payload = s_payload;
         const uint32_t gidx = payload >> 8, cta = payload & 255u;
+        const uint32_t stream = gidx >> P.cap_log2;
+        const uint32_t seq = s_seq;
+        const uint32_t slot = seq % W;
         const TaskRec *r = P.recs + gidx;
         if (threadIdx.x < 4)
             reinterpret_cast<uint4 *>(&s_hdr)[threadIdx.x] = __ldcg(reinterpret_cast<const uint4 *>(r) + threadIdx.x);
+        // wait until every upstream task still active at dispatch retired: the
+        // task in slot b is seq - ((seq - b) mod W); done words only grow
+        const unsigned long long up = s_up;
+        if (up && threadIdx.x < 32) {
+            const uint32_t *done = P.done + stream * kMaxWindow;
+            const bool w0 = (up >> lane) & 1ull, w1 = lane + 32 < W && ((up >> (lane + 32)) & 1ull);
+            const uint32_t i0 = seq - ((seq - lane + 64u * W) % W) + 1u;
+            const uint32_t i1 = seq - ((seq - lane - 32u + 64u * W) % W) + 1u;
+            uint32_t spins = 0, backoff = 16;
+            unsigned long long tw = 0;
+            while (true) {
+                bool ok = true;
+                if (w0) ok = (int32_t)(ld_relaxed_u32(&done[lane]) - i0) >= 0;
+                if (w1) ok = ok && (int32_t)(ld_relaxed_u32(&done[lane + 32]) - i1) >= 0;
+                if (__all_sync(0xffffffffu, ok)) { fence_acq_rel_gpu(); break; }
+                if ((++spins & 7) == 0) {
+                    const bool stop = stopped(P);
+                    const unsigned long long now = globaltimer_ns();
+                    if (tw == 0) tw = now;
+                    bool expired = now - tw > 4ull * P.timeout_ns;
+                    if (expired && lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
+                    if (__any_sync(0xffffffffu, stop || expired)) break;
+                }
+                __nanosleep(backoff);
+                if (backoff < 64) backoff <<= 1;
+            }
+        }
         __syncthreads();
-        const uint32_t stream = gidx >> P.cap_log2;
-        const uint32_t seq = s_hdr.seq;
-        const uint32_t slot = seq % P.window;
+        if (tracing && threadIdx.x == 0)
+            atomicMin(&P.trace[(((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))) * kTraceFields + 2],
+                      globaltimer_ns());
         if (logging && threadIdx.x == 0) {
             const unsigned long long t = atomicAdd(&P.ctl->ticket, 1ull);
             atomicMin(&P.log_start[((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))], t);
@@ -418,11 +721,19 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         run_body(s_hdr, (int)cta, smem, &P.ctl->stop);
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            uint32_t *cnt = &P.remaining[stream * kMaxWindow + slot];
-            const uint32_t before = atomicAdd(cnt, 1u);
-            if (before + 1u == (uint32_t)s_hdr.ncta) {
-                st_relaxed_u32(cnt, 0u);
+            bool last = true;
+            if (s_hdr.ncta > 1) {
+                // CTAs of one task count themselves; the last one resets the
+                // counter for the slot's next task and publishes completion
+                __threadfence();
+                uint32_t *cnt = &P.remaining[stream * kMaxWindow + slot];
+                last = atomicAdd(cnt, 1u) + 1u == (uint32_t)s_hdr.ncta;
+                if (last) st_relaxed_u32(cnt, 0u);
+            }
+            if (last) {
+                if (tracing)
+                    P.trace[(((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))) * kTraceFields + 3] =
+                        globaltimer_ns();
                 if (logging) {
                     const unsigned long long t = atomicAdd(&P.ctl->ticket, 1ull);
                     P.log_retire[((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))] = t;
@@ -435,10 +746,13 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
 
 // ---- kernels ----------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock, 4) acs_persistent_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(kBlock, 3) acs_persistent_kernel(const __grid_constant__ KParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (blockIdx.x < P.n_streams) {
+        sched_init(P, blockIdx.x, smem);
+        __syncthreads();
         if (threadIdx.x < 32) scheduler_warp(P, blockIdx.x, smem);
+        else checker_warp(P, blockIdx.x, smem, threadIdx.x / 32 - 1);
     } else {
         worker_loop(P, smem);
     }

@@ -60,9 +60,11 @@ struct acs_ctx {
     DevCtl *d_ctl = nullptr;
     uint32_t *d_done = nullptr, *d_remaining = nullptr;
     unsigned long long *d_cells = nullptr;
+    CellAux *d_cellaux = nullptr;
     uint32_t ncells = 0;
     unsigned long long *d_log_mask = nullptr, *d_log_start = nullptr, *d_log_retire = nullptr;
     SchedStats *d_sched_stats = nullptr;
+    unsigned long long *d_trace = nullptr;
     HostStatus *h_status = nullptr, *d_status = nullptr;
     std::vector<StreamState> st;
     int err = ACS_OK;
@@ -183,12 +185,14 @@ int flush_window(acs_ctx *c) {
     P.recs = c->d_ring;
     P.ctl = c->d_ctl;
     P.cells = c->d_cells;
+    P.cellaux = c->d_cellaux;
     P.done = c->d_done;
     P.remaining = c->d_remaining;
     P.log_mask = c->d_log_mask;
     P.log_start = c->d_log_start;
     P.log_retire = c->d_log_retire;
     P.sched_stats = c->d_sched_stats;
+    P.trace = c->d_trace;
     P.hstatus = c->d_status;
     P.timeout_ns = c->cfg.timeout_ns;
     P.cap_log2 = c->cap_log2;
@@ -198,6 +202,7 @@ int flush_window(acs_ctx *c) {
     P.n_streams = c->S;
     P.flags = c->cfg.flags;
     P.sched_smem = sched_smem_bytes(c->W);
+    P.poll_ns = c->cfg.poll_ns ? c->cfg.poll_ns : 128u;
     for (uint32_t s = 0; s < c->S; ++s) {
         P.first[s] = c->st[s].flushed;
         P.end[s] = c->st[s].submitted;
@@ -390,10 +395,12 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_done);
     cudaFree(c->d_remaining);
     cudaFree(c->d_cells);
+    cudaFree(c->d_cellaux);
     cudaFree(c->d_log_mask);
     cudaFree(c->d_log_start);
     cudaFree(c->d_log_retire);
     cudaFree(c->d_sched_stats);
+    cudaFree(c->d_trace);
     if (c->h_ring) cudaFreeHost(c->h_ring);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -463,8 +470,11 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     while (cells < std::min<uint32_t>(2u * window * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
     c->ncells = std::max<uint32_t>(cells, 4096);
     chk(cudaMalloc(&c->d_cells, (size_t)c->ncells * sizeof(unsigned long long)));
-    const size_t nlog = (cfg.flags & ACS_FLAG_LOG) ? (size_t)c->S * c->LC : 1;
-    if (!(cfg.flags & ACS_FLAG_LOG)) c->log_log2 = 0, c->LC = 1;
+    chk(cudaMalloc(&c->d_cellaux, (size_t)c->ncells * sizeof(CellAux)));
+    const bool keep_log = (cfg.flags & (ACS_FLAG_LOG | ACS_FLAG_TRACE)) != 0;
+    if (!keep_log) c->log_log2 = 0, c->LC = 1;
+    const size_t nlog = keep_log ? (size_t)c->S * c->LC : 1;
+    chk(cudaMalloc(&c->d_trace, nlog * kTraceFields * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_log_mask, nlog * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_log_start, nlog * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_log_retire, nlog * sizeof(unsigned long long)));
@@ -479,6 +489,14 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
 
     // grid: one scheduler CTA per stream + worker CTAs, all co-resident
     c->smem = dyn_smem_bytes(window);
+    if (cfg.ctas_per_sm) {
+        // reserve enough shared memory that at most ctas_per_sm CTAs fit an SM
+        int per_sm_smem = 0, per_block_optin = 0;
+        chk(cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+        chk(cudaDeviceGetAttribute(&per_block_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        const uint32_t want = (uint32_t)per_sm_smem / (cfg.ctas_per_sm + 1) + 1024u;
+        c->smem = std::max<uint32_t>(c->smem, std::min<uint32_t>(want, (uint32_t)per_block_optin));
+    }
     const void *kfn = persistent_kernel_fn();
     chk(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
     int per_sm = 0, sms = 0;
@@ -700,16 +718,37 @@ int acs_get_log(acs_ctx *c, uint32_t stream, uint64_t first, uint32_t n, uint64_
     return ACS_OK;
 }
 
+int acs_get_trace(acs_ctx *c, uint32_t stream, uint64_t first, uint32_t n, uint64_t *t) {
+    if (!c || !t || stream >= c->S || !(c->cfg.flags & ACS_FLAG_TRACE)) return ACS_ERR_INVALID;
+    const StreamState &ss = c->st[stream];
+    if (first + n > ss.synced || n > c->LC || first + c->LC < ss.synced) return ACS_ERR_INVALID;
+    uint64_t a = first, done = 0;
+    while (done < n) {
+        const uint64_t pa = a & (c->LC - 1);
+        const uint64_t m = std::min<uint64_t>(n - done, c->LC - pa);
+        cudaError_t e = cudaMemcpy(t + done * kTraceFields, c->d_trace + ((size_t)stream * c->LC + pa) * kTraceFields,
+                                   m * kTraceFields * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return ACS_ERR_DEVICE;
+        a += m;
+        done += m;
+    }
+    return ACS_OK;
+}
+
 int acs_get_stats(acs_ctx *c, acs_stats *out) {
     if (!c || !out) return ACS_ERR_INVALID;
     if (c->cfg.mode == ACS_MODE_WINDOW) {
         std::vector<SchedStats> ss(c->S);
         if (cudaMemcpy(ss.data(), c->d_sched_stats, c->S * sizeof(SchedStats), cudaMemcpyDeviceToHost) == cudaSuccess) {
             c->stats.sched_cycles = c->stats.sched_busy_cycles = c->stats.sched_inserts = 0;
+            c->stats.sched_iterations = 0;
+            for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] = 0;
             for (auto &x : ss) {
+                for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] += x.phase[k];
                 c->stats.sched_cycles += x.cycles;
                 c->stats.sched_busy_cycles += x.busy_cycles;
                 c->stats.sched_inserts += x.inserts;
+                c->stats.sched_iterations += x.iterations;
             }
         }
     }

@@ -120,7 +120,8 @@ class Context:
     """An acs_ctx on the current torch CUDA stream (raises on every error)."""
 
     def __init__(self, window: int, mode: str = "window", n_streams: int = 1, cta_slots: int = 0,
-                 capacity: int = 0, log: bool = False, timing: bool = False, timeout_s: float = 5.0,
+                 capacity: int = 0, log: bool = False, timing: bool = False, trace: bool = False,
+                 timeout_s: float = 5.0, poll_ns: int = 0, ctas_per_sm: int = 0,
                  cuda_stream: Optional[int] = None):
         cfg = acs.acs_config_default()
         cfg.mode = MODES[mode]
@@ -128,8 +129,11 @@ class Context:
         cfg.cta_slots = cta_slots
         if capacity:
             cfg.capacity = capacity
-        cfg.flags = (acs.ACS_FLAG_LOG if log else 0) | (acs.ACS_FLAG_TIMING if timing else 0)
+        cfg.flags = ((acs.ACS_FLAG_LOG if log else 0) | (acs.ACS_FLAG_TIMING if timing else 0)
+                     | (acs.ACS_FLAG_TRACE if trace else 0))
         cfg.timeout_ns = int(timeout_s * 1e9)
+        cfg.poll_ns = poll_ns
+        cfg.ctas_per_sm = ctas_per_sm
         cfg.cuda_stream = C.c_void_p(cuda_stream if cuda_stream is not None
                                      else torch.cuda.current_stream().cuda_stream)
         self.window, self.mode, self.n_streams = window, mode, n_streams
@@ -152,6 +156,9 @@ class Context:
 
     def log(self, stream: int, first: int, n: int):
         return acs.acs_get_log(self.h, stream, first, n)
+
+    def trace(self, stream: int, first: int, n: int) -> np.ndarray:
+        return acs.acs_get_trace(self.h, stream, first, n)
 
     def stats(self) -> dict:
         return acs.stats_dict(acs.acs_get_stats(self.h))
