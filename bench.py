@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the window scheduler on the rigid-sphere RL-simulation stream.
+
+One bench step = one complete run of the stream: 256 environments x 32 spheres,
+50 simulation steps, window 32, about 300 small tasks (1-16 CTAs) per
+simulation step whose task graph depends on the simulated contacts. Per
+simulation step the host submits one batch through the C ABI, flushes, syncs
+and reads back the island counts (1 KiB) the broadphase tasks wrote, which
+decide the next batch's tasks.
+
+Prints ONE JSON line (rank 0). Arms measured on the same box and workload:
+  value                  window scheduler (acs_flush -> persistent kernel)
+  inorder                one kernel launch per task on one stream
+  graph_launch           CUDA graph of each batch's full DAG, launch time only
+  graph_with_build       same, including host DAG build + instantiate
+``--impl reference`` times the CPU oracle (in-order executor) instead.
+
+Timing: CUDA events on the library's stream around each bench step, L2
+flushed (512 MiB write) between timed steps, W >= 3 warm-up steps; nvidia-smi
+clocks sampled during the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
+WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["acs", "reference"], default="acs")
+    ap.add_argument("--window", type=int, default=32)
+    ap.add_argument("--cta-slots", type=int, default=0)
+    ap.add_argument("--no-baselines", action="store_true", help="skip the in-order / graph arms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def rl_params(steps=50):
+    import streamgen as sg
+    return sg.RLParams(n_env=256, steps=steps)
+
+
+# ---- CPU oracle ---------------------------------------------------------------------
+
+def cpu_oracle_rate(budget_s: float = 10.0, max_runs: int = 20):
+    """The oracle's in-order executor on full runs of the same stream."""
+    import streamgen as sg
+    from oracle import execute
+    execute.build_c()
+    tasks = 0
+    runs = 0
+    t0 = time.perf_counter()
+    while runs < max_runs and (time.perf_counter() - t0) < budget_s:
+        t, _, _ = execute.run_rlsim(sg.RLSim(1 + runs, rl_params()))
+        tasks += len(t)
+        runs += 1
+    dt = time.perf_counter() - t0
+    return {"value": tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full runs of the stream (256 envs x 32 spheres x 50 steps, {tasks} tasks), "
+                      f"single-threaded numpy + C bodies, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import streamgen as sg
+    from oracle import execute
+    execute.build_c()
+    for w in range(args.warmup):
+        execute.run_rlsim(sg.RLSim(100 + w, rl_params(steps=5)))
+    times, tasks = [], 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        t, _, _ = execute.run_rlsim(sg.RLSim(1 + k, rl_params()))
+        times.append(time.perf_counter() - t0)
+        tasks = len(t)
+    ms = 1e3 * statistics.mean(times)
+    value = tasks / (ms / 1e3)
+    cores = 1
+    line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step one full run of the stream ({tasks} tasks), single-threaded"},
+            "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- clocks ---------------------------------------------------------------------------
+
+REASONS = ["clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+           "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = "index,clocks.sm,clocks.max.sm,power.draw," + ",".join(REASONS)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except OSError:
+            rows = []
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for name, v in zip(REASONS, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name.split(".")[-1])
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- GPU arms ----------------------------------------------------------------------------
+
+class RLBench:
+    """One mode (window / inorder / graph) on one device state."""
+
+    def __init__(self, mode, seed, window, cta_slots, timing=True):
+        import torch
+        import streamgen as sg
+        from paper_2401_12377_b300 import harness
+        self.torch = torch
+        self.sim = sg.RLSim(seed, rl_params())
+        host = self.sim.buffers()
+        self.bufs = harness.DeviceBuffers(host)
+        self.pristine = {k: v.clone() for k, v in self.bufs.t.items()}
+        self.host_pinned = {k: torch.from_numpy(v.view("uint8").copy()).pin_memory() for k, v in host.items()}
+        self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots)
+        self.driver = harness.RLDriver(self.sim, self.bufs, self.ctx)
+        self.mode = mode
+
+    def reset_device(self):
+        for k, t in self.bufs.t.items():
+            t.copy_(self.pristine[k], non_blocking=True)
+
+    def upload_host(self):
+        for k, t in self.bufs.t.items():
+            t.copy_(self.host_pinned[k], non_blocking=True)
+
+    def run_once(self, latencies=None):
+        """One full stream; returns tasks submitted."""
+        before = self.ctx.stats()["tasks_submitted"]
+        plan = self.sim.first_plan()
+        steps = self.sim.p.steps
+        for t in range(steps + 1):
+            t0 = time.perf_counter()
+            if t > 0:
+                plan = self.sim.step_plan(t - 1, self.driver.read_nisl())
+            self.ctx.submit_packed(*self.driver.pack(plan))
+            self.ctx.flush()
+            self.ctx.sync()
+            if latencies is not None:
+                latencies.append(time.perf_counter() - t0)
+        return self.ctx.stats()["tasks_submitted"] - before
+
+
+def l2_flush(buf):
+    buf.zero_()
+
+
+def time_arm(arm, steps, warmup, flush_buf, latencies=None):
+    torch = arm.torch
+    for _ in range(warmup):
+        arm.reset_device()
+        arm.run_once()
+    torch.cuda.synchronize()
+    st0 = arm.ctx.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    tasks = 0
+    wall = 0.0
+    for k in range(steps):
+        arm.reset_device()
+        l2_flush(flush_buf)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        ev[k][0].record()
+        tasks += arm.run_once(latencies)
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        wall += time.perf_counter() - w0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st1 = arm.ctx.stats()
+    fixed = ("cta_slots", "grid")
+    delta = {k: (st1[k] - st0[k]) if isinstance(st1[k], (int, float)) and k not in fixed else st1[k] for k in st1}
+    return {"ms": ms, "tasks": tasks, "wall_s": wall, "stats": delta}
+
+
+def time_e2e(arm, steps):
+    """Host buffers in, results out: H2D of the initial state from pinned
+    memory, the run, D2H of the final pos / vel, all inside CUDA events."""
+    torch = arm.torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out_pos = torch.empty_like(arm.bufs.t["pos"], device="cpu").pin_memory()
+    out_vel = torch.empty_like(arm.bufs.t["vel"], device="cpu").pin_memory()
+    tasks = 0
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        arm.upload_host()
+        tasks += arm.run_once()
+        out_pos.copy_(arm.bufs.t["pos"], non_blocking=True)
+        out_vel.copy_(arm.bufs.t["vel"], non_blocking=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    h2d_inputs = sum(t.numel() for t in arm.host_pinned.values())
+    n_flush = arm.sim.p.steps + 1
+    desc_bytes = (tasks // steps) * 320
+    d2h = out_pos.numel() + out_vel.numel() + arm.sim.p.steps * arm.sim.p.n_env * 4
+    return {"value": (tasks / steps) / (ms / 1e3), "unit": "tasks/s",
+            "h2d_bytes_per_step": int(h2d_inputs + desc_bytes), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": ms, "flushes_per_step": n_flush}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2401_12377_b300 import build
+    build.build()
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
+        try:
+            peaks = json.load(f)
+            peak_src = "measured"
+        except json.JSONDecodeError:
+            peaks, peak_src = {"hbm_gbs": 6400.0}, "fallback"
+
+    # one non-default stream for all of this process's device work: torch
+    # copies (state resets, L2 flush, read-backs) and the library's launches
+    torch.cuda.set_stream(torch.cuda.Stream())
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    seed = 1 + rank
+
+    # ---- the method ------------------------------------------------------------------
+    acs_arm = RLBench("window", seed, args.window, args.cta_slots)
+    latencies = []
+    if dist:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = time_arm(acs_arm, args.steps, args.warmup, flush_buf, latencies)
+    clocks = clk.summary()
+    ms_step = statistics.mean(res["ms"])
+    tasks_per_step = res["tasks"] / args.steps
+    max_ms = ms_step
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    value = world * tasks_per_step / (max_ms / 1e3)
+    st = res["stats"]
+    launches = st["launches"]
+    kernel_ms = st["kernel_ms"]
+    avg_launch_s = (kernel_ms / 1e3) / max(1, launches)
+    bytes_per_launch = st["seg_bytes"] / max(1, launches)
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    lat_us = sorted(1e6 * x for x in latencies)
+
+    line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "window": args.window, "tasks_per_step": tasks_per_step,
+                       "flushes_per_step": acs_arm.sim.p.steps + 1, "cta_slots": st.get("cta_slots"),
+                       "grid": st.get("grid"), "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
+            "sim_step_latency_us": {"p50": lat_us[len(lat_us) // 2] if lat_us else None,
+                                    "p99": lat_us[min(len(lat_us) - 1, int(0.99 * len(lat_us)))] if lat_us else None},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "acs_persistent_kernel", "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "avg_launch_us": avg_launch_s * 1e6,
+                         "note": "bytes named by the tasks' read+write segments per launch / mean "
+                                 "launch time (CUDA events around each cooperative launch)"},
+            "sched_cycles_per_task": st["sched_cycles"] / max(1, st["sched_inserts"]),
+            "gpu_launches": int(launches),
+            "clocks": clocks}
+
+    # ---- baselines on the same box -----------------------------------------------------------
+    if not args.no_baselines:
+        inorder = RLBench("inorder", seed, args.window, args.cta_slots)
+        r_in = time_arm(inorder, args.steps, max(1, args.warmup // 2), flush_buf)
+        ms_in = statistics.mean(r_in["ms"])
+        graph = RLBench("graph", seed, args.window, args.cta_slots)
+        r_g = time_arm(graph, args.steps, max(1, args.warmup // 2), flush_buf)
+        ms_g = statistics.mean(r_g["ms"])
+        g_launch_ms = r_g["stats"]["kernel_ms"] / args.steps
+        g_build_ms = (r_g["stats"]["graph_build_ms"] + r_g["stats"]["graph_instantiate_ms"]) / args.steps
+        line["inorder"] = {"tasks_per_s": tasks_per_step / (ms_in / 1e3), "ms_per_step": ms_in}
+        line["graph_with_build"] = {"tasks_per_s": tasks_per_step / (ms_g / 1e3), "ms_per_step": ms_g,
+                                    "host_build_instantiate_ms_per_step": g_build_ms}
+        line["graph_launch"] = {"tasks_per_s": tasks_per_step / (g_launch_ms / 1e3),
+                                "device_ms_per_step": g_launch_ms,
+                                "note": "sum of graph launch device times only (build excluded, "
+                                        "host round trips between graphs excluded)"}
+        line["speedup_vs_inorder"] = ms_in / ms_step
+        line["speedup_vs_graph_with_build"] = ms_g / ms_step
+        line["speedup_vs_graph_launch_only"] = g_launch_ms / ms_step
+        line["acs_kernel_ms_per_step"] = kernel_ms / args.steps
+        line["speedup_kernel_time_vs_graph_launch"] = g_launch_ms / (kernel_ms / args.steps)
+        inorder.ctx.close()
+        graph.ctx.close()
+
+    # ---- end to end through the API with host buffers ---------------------------------------
+    line["e2e"] = time_e2e(acs_arm, max(1, min(args.steps, 3)))
+    acs_arm.ctx.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate()
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -59,7 +59,7 @@ struct alignas(128) DevCtl {
     uint32_t sched_done;    // scheduler warps that finished their streams
     uint32_t exit_count;    // CTAs that left the kernel
     uint32_t err;           // first error (ACS_ERR_*), 0 = none
-    uint32_t err_info;      // where: 1 scheduler, 2 worker, 3 producer ring, 4 prefetch
+    uint32_t err_info;      // where: enum ErrSite
     uint32_t pad2[27];
     unsigned long long ticket;  // legality-log ticket counter
     uint32_t pad3[30];
@@ -129,7 +129,7 @@ __host__ __device__ inline uint32_t hist_size(uint32_t window) { return window <
 
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    return H * (uint32_t)sizeof(TaskRec) + H * 8 + H * 4 + (H / kPrefetch) * 8 + 16 + 32 * 24;
+    return H * (uint32_t)sizeof(TaskRec) + H * 8 + H * 4 + 16 + 32 * 24;
 }
 
 inline uint32_t dyn_smem_bytes(uint32_t window) {
@@ -141,6 +141,10 @@ inline uint32_t dyn_smem_bytes(uint32_t window) {
 enum SlotState : uint32_t { kEmpty = 0, kPending = 1, kReady = 2, kExec = 3, kRetired = 4 };
 
 // error-site codes stored in DevCtl::err_info
-enum ErrSite : uint32_t { kSiteSched = 1, kSiteWorker = 2, kSiteRing = 3, kSitePrefetch = 4 };
+enum ErrSite : uint32_t {
+    kSiteSched = 1, kSiteWorker = 2, kSiteRing = 3, kSitePrefetch = 4,
+    // self-checks (ACS_ERR_INVALID): a descriptor or work unit that is not what it must be
+    kSiteCheckRecord = 5, kSiteWorkerPayload = 6, kSiteWorkerRecord = 7
+};
 
 }  // namespace acs

@@ -3,13 +3,13 @@
 // CTAs [0, n_streams) are schedulers: warp 0 of CTA s owns stream s. It keeps
 // the stream's scheduling window (W slots, Sec. III-C) in shared memory and the
 // per-slot state machine (pending / ready / executing / retired, Sec. III-C) and
-// upstream masks in registers: lane l holds slots l and l + 32. Descriptors
-// stream into shared memory by bulk copy (cp.async.bulk + mbarrier) ahead of
-// use. Inserting a task runs the segment-overlap test of Alg. 1 (extended to
-// read-after-write) against all W - 1 earlier tasks in one warp step, one slot
-// per lane, and a ballot turns the per-lane results into the task's upstream
-// mask. Retirement clears one bit from every mask (mask &= ~retired); a ballot
-// of empty masks is the ready set, dispatched oldest first.
+// upstream masks in registers: lane l holds slots l and l + 32. Warp 7 streams
+// descriptors into a shared-memory history ring ahead of use; warps 1..6 run
+// the segment-overlap test of Alg. 1 (extended to read-after-write) of each
+// task against its W - 1 predecessors, one predecessor per lane, and a ballot
+// turns the per-lane results into the task's upstream-candidate mask. Warp 0
+// inserts checked tasks (upstream = candidates still active), retires them
+// (mask &= ~retired) and dispatches them oldest first.
 //
 // CTAs [n_streams, grid) are workers: each claims work-ring positions one at a
 // time, runs the body for one (task, CTA index) unit, and the last CTA of a
@@ -49,52 +49,6 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -113,22 +67,21 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 // ---- scheduler CTA ----------------------------------------------------------------
 //
 // Shared memory of a scheduler CTA (stream s):
-//   hist[H]     the descriptors of tasks seq mod H, streamed in by bulk copy in
-//               batches of kPrefetch aligned to kPrefetch; it holds the W - 1
-//               predecessors of every task still to be checked
+//   hist[H]     the descriptors of tasks seq mod H, copied in by the loader
+//               warp in batches of kPrefetch aligned to kPrefetch; it holds the
+//               W - 1 predecessors of every task still to be checked
 //   pmask[H]    upstream-candidate mask of task seq mod H (bit i mod W for
 //               each conflicting predecessor i in [seq - W + 1, seq - 1])
 //   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
-//   bar[H/16]   one mbarrier per batch position of hist
 //   sh          counters shared by the warps
 //
-// Warps 1..7 ("checkers") compute pmask for tasks j = first + w - 1 + 7k: the
+// Warps 1..6 ("checkers") compute pmask for tasks j = first + w + 6k: the
 // segment-overlap test of Alg. 1 (extended to RAW) of task j against its W - 1
 // predecessors, one predecessor per lane, ballot -> mask. The candidate set of
 // a task is fixed by the stream, so the test runs ahead of execution, in
-// parallel with it. Warp 0 owns the state machine: it loads descriptors,
-// inserts checked tasks into the W-slot ring (upstream = pmask & active slots),
-// polls completion, releases slots in program order and dispatches.
+// parallel with it. Warp 7 loads descriptors. Warp 0 owns the state machine:
+// it inserts checked tasks into the W-slot ring (upstream = pmask & active
+// slots), polls completion, releases slots in program order and dispatches.
 
 struct SchedShared {
     uint32_t complete_upto;  // hist holds every seq below (loaded), from `lo`
@@ -150,7 +103,6 @@ struct SchedSmem {
     TaskRec *hist;
     unsigned long long *pmask;
     uint32_t *ptag;
-    uint64_t *bar;
     SchedShared *sh;
     uint32_t H;
 };
@@ -165,8 +117,6 @@ __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     p += s.H * sizeof(unsigned long long);
     s.ptag = reinterpret_cast<uint32_t *>(p);
     p += s.H * sizeof(uint32_t);
-    s.bar = reinterpret_cast<uint64_t *>(p);
-    p += (s.H / kPrefetch) * sizeof(uint64_t);
     s.sh = reinterpret_cast<SchedShared *>(p);
     p += sizeof(SchedShared);
     s.disp = reinterpret_cast<DispatchEntry *>(p);
@@ -179,7 +129,7 @@ __device__ __forceinline__ void sts_volatile(uint32_t *p, uint32_t v) { *(volati
 // Alg. 1's overlap test between task i (earlier) and task j on inclusive
 // ranges; a segment pair counts unless both are reads (RAW, WAR, WAW).
 __device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const TaskRec &rj) {
-    const int ni = ri.nseg, nj = rj.nseg;
+    const int ni = min((int)ri.nseg, kMaxSegs), nj = min((int)rj.nseg, kMaxSegs);
     const uint32_t wi = ri.wmask, wj = rj.wmask;
     for (int y = 0; y < ni; ++y) {
         const Seg b = ri.seg[y];
@@ -192,13 +142,59 @@ __device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const TaskRec &r
     return false;
 }
 
+// Warp 7: copies descriptors from the stream's device ring into hist with
+// ordinary loads, a batch of kPrefetch at a time, and publishes them through
+// complete_upto after a CTA-scope fence. hist[s mod H] may take seq s once the
+// record it replaces (s - H) is neither a candidate of an unchecked task nor
+// uninserted: s < next + H - W + 1.
+__device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t W = P.window;
+    const uint32_t C = 1u << P.cap_log2;
+    const uint32_t first = P.first[stream], end = P.end[stream];
+    const TaskRec *recs = P.recs + (size_t)stream * C;
+    SchedSmem S = carve(smem_raw, W);
+    const uint32_t H = S.H, HM = H - 1;
+    uint32_t load_upto = first > W - 1 ? first - (W - 1) : 0u;
+    unsigned long long tw = 0;
+    uint32_t spins = 0, backoff = 32;
+    while (load_upto < end) {
+        const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
+        const uint32_t nx = lds_volatile(&S.sh->next);
+        if (bhi + W > nx + H + 1) {
+            if (lds_volatile(&S.sh->quit)) return;
+            if ((++spins & 63) == 0) {
+                const unsigned long long now = globaltimer_ns();
+                if (tw == 0) tw = now;
+                else if (now - tw > 4ull * P.timeout_ns) {
+                    if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSitePrefetch);
+                    return;
+                }
+            }
+            __nanosleep(backoff);
+            if (backoff < 256) backoff <<= 1;
+            continue;
+        }
+        tw = 0;
+        backoff = 32;
+        const uint32_t n16 = (bhi - load_upto) * (uint32_t)(sizeof(TaskRec) / 16);
+        const uint4 *src = reinterpret_cast<const uint4 *>(recs + (load_upto & (C - 1)));
+        uint4 *dst = reinterpret_cast<uint4 *>(&S.hist[load_upto & HM]);
+        for (uint32_t i = lane; i < n16; i += 32) dst[i] = __ldcg(src + i);
+        __syncwarp();
+        __threadfence_block();
+        load_upto = bhi;
+        if (lane == 0) sts_volatile(&S.sh->complete_upto, load_upto);
+    }
+}
+
 __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw, uint32_t w) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     const uint32_t first = P.first[stream], end = P.end[stream];
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
-    constexpr uint32_t kCheckers = kBlock / 32 - 1;
+    constexpr uint32_t kCheckers = kBlock / 32 - 2;   // warps 1 .. 6
     unsigned long long tw = 0;
     for (uint32_t j = first + w; j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
@@ -222,6 +218,10 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         tw = 0;
         __threadfence_block();
         const TaskRec &rj = S.hist[j & HM];
+        if (rj.seq != j || rj.nseg > kMaxSegs) {   // self-check: the record must be task j
+            if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteCheckRecord);
+            return;
+        }
         bool c0 = false, c1 = false;
         const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
         if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM], rj);
@@ -255,12 +255,10 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     const uint32_t first = P.first[stream];
     SchedSmem S = carve(smem_raw, W);
     for (uint32_t i = threadIdx.x; i < S.H; i += blockDim.x) S.ptag[i] = 0;
-    if (threadIdx.x < S.H / kPrefetch) mbar_init(&S.bar[threadIdx.x], 1);
     if (threadIdx.x == 0) {
         S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
         S.sh->next = first;
         S.sh->quit = 0;
-        fence_mbar_init();
     }
 }
 
@@ -269,14 +267,13 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const uint32_t W = P.window;
     const uint32_t C = 1u << P.cap_log2;
     const uint32_t first = P.first[stream], end = P.end[stream];
-    const TaskRec *recs = P.recs + (size_t)stream * C;
     uint32_t *done = P.done + stream * kMaxWindow;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const uint32_t LM = (1u << P.log_log2) - 1u;
     const size_t lbase = (size_t)stream << P.log_log2;
     SchedSmem S = carve(smem_raw, W);
-    const uint32_t H = S.H, HM = H - 1, NB = H / kPrefetch;
+    const uint32_t H = S.H, HM = H - 1;
     const unsigned long long t_begin = clock64();
     unsigned long long busy = 0, inserts = 0;
 
@@ -284,9 +281,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     uint32_t st0 = kEmpty, st1 = kEmpty, sq0 = 0, sq1 = 0, nc0 = 0, nc1 = 0;
     unsigned long long mk0 = 0, mk1 = 0;
 
-    const uint32_t lo = first > W - 1 ? first - (W - 1) : 0u;   // oldest record loaded
-
-    uint32_t load_upto = lo, complete_upto = lo, bph = 0;  // bph: parity bit per barrier
     uint32_t head = first, next = first;
     uint32_t hslot = first % W, nslot = first % W;   // head % W, next % W
     const bool sole_producer = P.n_streams == 1;
@@ -307,30 +301,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         bool progress = false;
         const unsigned long long t0 = clock64();
         tp = t0;
-
-        // 0. stream descriptors into hist (never over a record still needed)
-        while (load_upto < end) {
-            // hist[s mod H] may take seq s once s - H is neither a candidate
-            // of an unchecked task nor uninserted: s < next + H - W + 1
-            const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
-            if (bhi + W > next + H + 1) break;
-            if (lane == 0) {
-                const uint32_t bytes = (bhi - load_upto) * (uint32_t)sizeof(TaskRec);
-                uint64_t *bar = &S.bar[(load_upto / kPrefetch) % NB];
-                fence_proxy_async();
-                mbar_expect_tx(bar, bytes);
-                bulk_g2s(&S.hist[load_upto & HM], recs + (load_upto & (C - 1)), bytes, bar);
-            }
-            load_upto = bhi;
-        }
-        while (complete_upto < load_upto) {
-            const uint32_t x = (complete_upto / kPrefetch) % NB;
-            if (!mbar_test_wait(&S.bar[x], (bph >> x) & 1u)) break;
-            bph ^= 1u << x;
-            complete_upto = min((complete_upto / kPrefetch + 1) * kPrefetch, end);
-            __threadfence_block();
-            if (lane == 0) sts_volatile(&S.sh->complete_upto, complete_upto);
-        }
 
         ACS_PHASE(0);
         // 1. how many tasks are checked and have a free slot (at most 32 per
@@ -598,22 +568,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     (void)failed;
     if (sole_producer && lane == 0) st_relaxed_u32(&P.ctl->ring_tail, tail);
     if (lane == 0) sts_volatile(&S.sh->quit, 1u);
-    // drain bulk copies still in flight before the CTA may exit
-    while (complete_upto < load_upto) {
-        const uint32_t x = (complete_upto / kPrefetch) % NB;
-        const unsigned long long tw = globaltimer_ns();
-        bool ok = true;
-        while (!mbar_try_wait(&S.bar[x], (bph >> x) & 1u)) {
-            if (globaltimer_ns() - tw > P.timeout_ns) {
-                if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSitePrefetch);
-                ok = false;
-                break;
-            }
-        }
-        if (!ok) break;
-        bph ^= 1u << x;
-        complete_upto = min((complete_upto / kPrefetch + 1) * kPrefetch, end);
-    }
     if (lane == 0) {
         SchedStats *ss = &P.sched_stats[stream];
         ss->cycles += clock64() - t_begin;
@@ -681,6 +635,10 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         const uint32_t seq = s_seq;
         const uint32_t slot = seq % W;
         const TaskRec *r = P.recs + gidx;
+        if (gidx >= (P.n_streams << P.cap_log2)) {   // self-check: payload names a ring entry
+            if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerPayload);
+            continue;
+        }
         if (threadIdx.x < 4)
             reinterpret_cast<uint4 *>(&s_hdr)[threadIdx.x] = __ldcg(reinterpret_cast<const uint4 *>(r) + threadIdx.x);
         // wait until every upstream task still active at dispatch retired: the
@@ -711,6 +669,11 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             }
         }
         __syncthreads();
+        if (s_hdr.seq != seq || cta >= s_hdr.ncta) {     // self-check: the unit matches its record
+            if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerRecord);
+            __syncthreads();
+            continue;
+        }
         if (tracing && threadIdx.x == 0)
             atomicMin(&P.trace[(((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))) * kTraceFields + 2],
                       globaltimer_ns());
@@ -751,8 +714,10 @@ __global__ void __launch_bounds__(kBlock, 3) acs_persistent_kernel(const __grid_
     if (blockIdx.x < P.n_streams) {
         sched_init(P, blockIdx.x, smem);
         __syncthreads();
-        if (threadIdx.x < 32) scheduler_warp(P, blockIdx.x, smem);
-        else checker_warp(P, blockIdx.x, smem, threadIdx.x / 32 - 1);
+        const uint32_t warp = threadIdx.x / 32;
+        if (warp == 0) scheduler_warp(P, blockIdx.x, smem);
+        else if (warp == kBlock / 32 - 1) loader_warp(P, blockIdx.x, smem);
+        else checker_warp(P, blockIdx.x, smem, warp - 1);
     } else {
         worker_loop(P, smem);
     }

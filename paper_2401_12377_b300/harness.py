@@ -134,8 +134,21 @@ class Context:
         cfg.timeout_ns = int(timeout_s * 1e9)
         cfg.poll_ns = poll_ns
         cfg.ctas_per_sm = ctas_per_sm
-        cfg.cuda_stream = C.c_void_p(cuda_stream if cuda_stream is not None
-                                     else torch.cuda.current_stream().cuda_stream)
+        # All device work of the context goes to one stream shared with torch, so
+        # torch copies of the task buffers are ordered with the tasks. The legacy
+        # default stream has no handle to share: then a torch stream is made
+        # current for the context's lifetime.
+        self._prev_stream = None
+        if cuda_stream is None:
+            cur = torch.cuda.current_stream()
+            if cur.cuda_stream == 0:
+                torch.cuda.synchronize()
+                self._prev_stream = cur
+                self._stream = torch.cuda.Stream()
+                torch.cuda.set_stream(self._stream)
+                cur = self._stream
+            cuda_stream = cur.cuda_stream
+        cfg.cuda_stream = C.c_void_p(cuda_stream)
         self.window, self.mode, self.n_streams = window, mode, n_streams
         self.h = acs.acs_init(window, cfg)
 
@@ -170,6 +183,10 @@ class Context:
         if self.h:
             acs.acs_destroy(self.h)
             self.h = None
+        if self._prev_stream is not None:
+            torch.cuda.synchronize()
+            torch.cuda.set_stream(self._prev_stream)
+            self._prev_stream = None
 
     def __enter__(self):
         return self
