@@ -280,6 +280,39 @@ int acs_get_stats(acs_ctx *ctx, acs_stats *out);
  * prebuilt graph; re-runs its tasks). Errors: ACS_ERR_INVALID if none. */
 int acs_graph_replay(acs_ctx *ctx);
 
+/*
+ * acs_run_noalloc -- run one stream of tasks without allocating anything.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they run their tasks, e.g. code executing
+ * during CUDA graph capture (allocation is not capturable), code embedded in a
+ * framework that owns the memory budget, or paths that cannot absorb an
+ * allocator's latency or failure. It runs the same persistent scheduler kernel
+ * as acs_flush (window of `window` slots, one stream, tasks in program order
+ * with the segments acs_get_addresses derives), but every byte of scratch
+ * comes from one fixed-size array in the library's device memory that every
+ * GPU loading the library holds until exit (under 2 MiB).
+ *
+ *   window      1 .. ACS_MAX_WINDOW
+ *   n           number of tasks, 0 .. ACS_NOALLOC_MAX_TASKS (more: ACS_ERR_INVALID)
+ *   task_ids    n strictly increasing ids (host memory)
+ *   args        n packed tasks (host memory); their pointers name the caller's
+ *               device buffers, which are the inputs and outputs
+ *   cuda_stream cudaStream_t to run on (NULL: the legacy default stream)
+ *
+ * Blocks until the tasks retired; returns ACS_OK or the first error
+ * (ACS_ERR_INVALID / ACS_ERR_ORDER for bad tasks, ACS_ERR_TIMEOUT,
+ * ACS_ERR_DEVICE). The first call on a device resolves the array's device
+ * address and sets the kernel's attributes with that device current: make it
+ * before any stream capture. Calls share the array (each re-initialises what
+ * must start at zero); calls whose device work overlaps race on it and must not
+ * be made. Not thread-safe. Calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ */
+#define ACS_NOALLOC_MAX_TASKS 4096
+int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task_ids, const acs_args *args,
+                    void *cuda_stream);
+
 /* The context's sticky error (ACS_OK if none). */
 int acs_error(const acs_ctx *ctx);
 

@@ -30,6 +30,7 @@ ACS_MAX_NCTA = 256
 ACS_MAX_STREAMS = 256
 ACS_BLOCK_THREADS = 256
 ACS_WHOLE_MEMORY = (0, (1 << 64) - 1)
+ACS_NOALLOC_MAX_TASKS = 4096
 
 OPS = {"nop": 0, "axpy": 1, "scale": 2, "add": 3, "gemv": 4, "bias_relu": 5, "resid": 6,
        "rl_broadphase": 10, "rl_solve": 11, "rl_integrate": 12, "wait_flag": 30, "sleep": 31}
@@ -73,7 +74,7 @@ assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
            "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_get_stats", "acs_graph_replay",
-           "acs_error", "acs_strerror", "acs_destroy"]
+           "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc"]
 
 _lib = None
 
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
     lib.acs_error.argtypes = [C.c_void_p]
     lib.acs_strerror.argtypes = [C.c_int]
     lib.acs_strerror.restype = C.c_char_p
+    lib.acs_run_noalloc.argtypes = [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.acs_destroy.argtypes = [C.c_void_p]
     lib.acs_destroy.restype = None
     for name in EXPORTS:
@@ -216,6 +218,14 @@ def acs_error(ctx) -> int:
 
 def acs_strerror(code: int) -> str:
     return load().acs_strerror(code).decode()
+
+
+def acs_run_noalloc(window: int, task_ids: np.ndarray, packed: np.ndarray, cuda_stream: int = 0) -> int:
+    """Run the packed tasks with the library's fixed scratch (no allocation)."""
+    ids = np.ascontiguousarray(task_ids, dtype=np.uint32)
+    packed = np.ascontiguousarray(packed)
+    assert packed.dtype == ARGS_DTYPE and len(packed) == len(ids)
+    return load().acs_run_noalloc(window, len(ids), ids.ctypes.data, packed.ctypes.data, cuda_stream)
 
 
 def acs_destroy(ctx) -> None:

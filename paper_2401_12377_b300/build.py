@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libacs.so")
-SOURCES = ["acs_kernels.cu", "acs_runtime.cu"]
+SOURCES = ["acs_kernels.cu", "acs_runtime.cu", "acs_noalloc.cu"]
 HEADERS = ["acs_internal.h", "acs_bodies.cuh"]
 
 NVCC_FLAGS = [
