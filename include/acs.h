@@ -84,6 +84,9 @@ enum acs_op {
     ACS_OP_RL_BROADPHASE = 10,/* sphere contacts + islands per env acs_rl_broadphase_args */
     ACS_OP_RL_SOLVE = 11,     /* Gauss-Seidel contact impulses, 1 env acs_rl_solve_args */
     ACS_OP_RL_INTEGRATE = 12, /* semi-implicit Euler + box walls   acs_rl_integrate_args */
+    ACS_OP_RL_EMIT = 13,      /* device-side task emission: append the next
+                                 simulation step's tasks to this task's own
+                                 stream from the island counts   acs_rl_emit_args */
     ACS_OP_WAIT_FLAG = 30,    /* test body: wait until *flag != 0, the stop flag, or
                                  limit_ns elapsed                  acs_wait_args */
     ACS_OP_SLEEP = 31         /* spin ns, then y[0] = y[0]*0.5 + tag (CTA 0)
@@ -118,6 +121,23 @@ typedef struct { uint64_t h, u, b; uint32_t n; uint32_t pad; } acs_resid_args;
 typedef struct { uint64_t pos, prop, cont, nisl; uint32_t nenv; uint32_t pad; } acs_rl_broadphase_args;
 typedef struct { uint64_t pos, prop, cont, vel; float beta_dt, slop; } acs_rl_solve_args;
 typedef struct { uint64_t pos, vel, prop; uint32_t nenv; float dt, gdt, box; } acs_rl_integrate_args;
+/* Device-side emission for the rigid-sphere stream. The emit task of step t
+ * reads the island counts of step t and appends, in this order: one
+ * ACS_OP_RL_SOLVE per environment with islands (ascending, ncta =
+ * clamp(islands, 1, 16)), one ACS_OP_RL_INTEGRATE per chunk of step t, and if
+ * t + 1 < steps one ACS_OP_RL_BROADPHASE per chunk of step t + 1 followed by
+ * the emit task of step t + 1. Appended tasks get task_id = their position in
+ * the stream. Chunk CTA counts come from ncta_table[(t * 2 + k) * n_chunks + c]
+ * (k = 0 broadphase of step t, k = 1 integrate of step t). Segments: reads
+ * nisl, the cfg block and the table; writes the 4-byte token (so emit tasks of
+ * one stream are ordered). A stream holding an emit task stays open until the
+ * last emit task ran: acs_sync returns once every appended task retired. */
+typedef struct {
+    uint64_t pos, vel, prop, cont;   /* device buffers of all environments */
+    float beta_dt, slop, dt, gdt, box;
+    uint32_t pad[3];
+} acs_rl_emit_cfg;                   /* device memory, read by emit tasks */
+typedef struct { uint64_t cfg, nisl, token, ncta_table; uint32_t n_env, step, steps, chunk; } acs_rl_emit_args;
 typedef struct { uint64_t flag; uint64_t limit_ns; } acs_wait_args;
 typedef struct { uint64_t y; uint64_t ns; float tag; uint32_t pad; } acs_sleep_args;
 
@@ -173,6 +193,8 @@ typedef struct acs_stats {
     uint64_t sched_phase_cycles[8]; /* scheduler-loop cycles by phase: descriptor loads,
                                    inserts, retire, dispatch selection, ring-cell checks,
                                    cell aux words, publication fence, cell stores */
+    uint64_t tasks_emitted;     /* tasks appended on the device by emit tasks */
+    uint64_t device_seg_bytes;  /* segment bytes of every checked task (host- or device-submitted) */
     uint32_t cta_slots;         /* worker CTAs of the persistent kernel */
     uint32_t grid;              /* total CTAs of the persistent kernel */
 } acs_stats;
@@ -210,8 +232,9 @@ int acs_get_addresses(const acs_args *args, acs_segment *reads, uint32_t *n_read
  * arrays. task_id must be strictly greater than the previous task_id of the
  * stream (it names the task in logs). At most ACS_MAX_SEGS non-empty segments.
  * Nothing runs until acs_flush.
- * Errors: ACS_ERR_INVALID, ACS_ERR_ORDER, ACS_ERR_FULL (more than
- * capacity - window + 1 tasks since the last acs_sync).
+ * Errors: ACS_ERR_INVALID (also: an emit task outside window mode, or a stream
+ * whose flushed emit tasks were not yet synced), ACS_ERR_ORDER, ACS_ERR_FULL
+ * (more than capacity - window + 1 tasks since the last acs_sync).
  */
 int acs_submit(acs_ctx *ctx, uint32_t task_id, const acs_args *args,
                const acs_segment *reads, uint32_t n_reads,

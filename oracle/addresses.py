@@ -34,6 +34,7 @@ OP_ROLES: Dict[str, Tuple[Tuple[str, ...], Tuple[str, ...]]] = {
     "rl_solve": (("pos", "prop", "cont", "vel"), ("vel",)),
     "rl_integrate": (("pos", "vel", "prop"), ("pos", "vel")),
     "sleep": ((), ("y",)),
+    "rl_emit": (("nisl",), ("token",)),
 }
 
 

@@ -79,6 +79,36 @@ def window_dag(E: Iterable[Tuple[int, int]], window: int) -> Set[Tuple[int, int]
     return {(i, j) for (i, j) in E if j - i <= window - 1}
 
 
+def window_dag_direct(segs, window: int) -> Set[Tuple[int, int]]:
+    """D_W built directly: the same conflict test, only over pairs at distance
+    at most W - 1 (for streams too long for the all-pairs E)."""
+    if window < 1:
+        raise ValueError("window must be >= 1")
+    D = set()
+    for j in range(len(segs)):
+        rj, wj = segs[j]
+        for i in range(max(0, j - window + 1), j):
+            ri, wi = segs[i]
+            if conflict(ri, wi, rj, wj):
+                D.add((i, j))
+    return D
+
+
+def check_release_order(start: Sequence[int], retire: Sequence[int], window: int) -> List[str]:
+    """Every task j starts after all tasks i <= j - W retired. With legality on
+    D_W this implies legality on all of E: every edge of E longer than W - 1 is
+    covered (the ring-window reading of Sec. IV-C's bounded window)."""
+    bad = []
+    run_max = -1
+    for j in range(len(start)):
+        i = j - window
+        if i >= 0:
+            run_max = max(run_max, retire[i])
+            if not run_max < start[j]:
+                bad.append(f"task {j}: starts at {start[j]} before task <= {i} retired ({run_max})")
+    return bad
+
+
 def check_legal(E: Iterable[Tuple[int, int]], start: Sequence[int], retire: Sequence[int]) -> List[str]:
     """Launch-legality of a ticketed execution log.
 

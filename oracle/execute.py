@@ -126,8 +126,8 @@ def run_task(bufs: Dict[str, np.ndarray], task) -> None:
                                 ctypes.c_float(S["gdt"]), ctypes.c_float(S["box"]))
         _view(bufs, A["pos"])[...] = pos
         _view(bufs, A["vel"])[...] = vel
-    elif op == "nop":
-        pass
+    elif op in ("nop", "rl_emit"):
+        pass        # an emit task changes the stream, not the buffers
     else:
         raise ValueError(f"unknown op {op!r}")
 
@@ -141,17 +141,22 @@ def run_inorder(buffers: Dict[str, np.ndarray], tasks, order=None) -> Dict[str, 
     return bufs
 
 
-def run_rlsim(sim):
+def run_rlsim(sim, emit: bool = False):
     """Run a ``streamgen.RLSim`` with the oracle: returns (tasks, buffers,
     batch_sizes). Each batch's tasks are emitted from the island counts the
-    oracle's own broadphase wrote into ``nisl``."""
-    bufs = {k: v.copy() for k, v in sim.buffers().items()}
+    oracle's own broadphase wrote into ``nisl``. With ``emit`` the stream is
+    the emitting variant: an emit task follows every broadphase batch."""
+    bufs = {k: v.copy() for k, v in sim.buffers(emit=emit).items()}
     tasks: List = []
     sizes = []
     batch = sim.first_batch()
+    if emit and sim.p.steps > 0:
+        batch.append(sim.emit_task(0))
     for t in range(sim.p.steps + 1):
         if t > 0:
             batch = sim.step_batch(t - 1, bufs["nisl"].copy())
+            if emit and t < sim.p.steps:
+                batch.append(sim.emit_task(t))
         for task in batch:
             run_task(bufs, task)
         tasks.extend(batch)

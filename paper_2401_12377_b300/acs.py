@@ -33,7 +33,8 @@ ACS_WHOLE_MEMORY = (0, (1 << 64) - 1)
 ACS_NOALLOC_MAX_TASKS = 4096
 
 OPS = {"nop": 0, "axpy": 1, "scale": 2, "add": 3, "gemv": 4, "bias_relu": 5, "resid": 6,
-       "rl_broadphase": 10, "rl_solve": 11, "rl_integrate": 12, "wait_flag": 30, "sleep": 31}
+       "rl_broadphase": 10, "rl_solve": 11, "rl_integrate": 12, "rl_emit": 13, "wait_flag": 30,
+       "sleep": 31}
 
 ACS_MODE_WINDOW, ACS_MODE_INORDER, ACS_MODE_GRAPH = 0, 1, 2
 ACS_FLAG_LOG, ACS_FLAG_TIMING, ACS_FLAG_TRACE = 1, 2, 4
@@ -64,7 +65,8 @@ class acs_stats(C.Structure):
                 ("graph_instantiate_ms", C.c_double), ("graph_edges", C.c_uint64),
                 ("sched_cycles", C.c_uint64), ("sched_busy_cycles", C.c_uint64),
                 ("sched_inserts", C.c_uint64), ("sched_iterations", C.c_uint64),
-                ("sched_phase_cycles", C.c_uint64 * 8), ("cta_slots", C.c_uint32),
+                ("sched_phase_cycles", C.c_uint64 * 8), ("tasks_emitted", C.c_uint64),
+                ("device_seg_bytes", C.c_uint64), ("cta_slots", C.c_uint32),
                 ("grid", C.c_uint32)]
 
 

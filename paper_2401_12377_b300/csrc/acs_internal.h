@@ -85,11 +85,22 @@ struct SchedStats {
     unsigned long long inserts;
     unsigned long long iterations;
     unsigned long long phase[kPhases];
+    unsigned long long seg_bytes;   // read + write segment bytes of the checked tasks
+    unsigned long long emitted;     // descriptors appended by device-side emitters
 };
 
 // per-task trace fields (globaltimer ns): insert, dispatch, first CTA start,
 // last CTA end, retirement seen by the scheduler
 constexpr int kTraceFields = 5;
+
+// Per-stream words shared by the scheduler and device-side emitters. A stream
+// holding emit tasks is open: its end grows as emitters append descriptors.
+struct StreamCtl {
+    uint32_t end;        // one past the last published descriptor
+    uint32_t open;       // emit tasks whose chain has not finished
+    uint32_t head_pub;   // oldest unreleased task (emitters wait for ring space)
+    uint32_t pad;
+};
 
 // Second word of a work-ring cell: the upstream slots the unit's worker must
 // still wait for (bit b: the task in window slot b) and the task's seq.
@@ -109,6 +120,7 @@ struct KParams {
     unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
     SchedStats *sched_stats;  // [n_streams]
     unsigned long long *trace;  // [n_streams][log_capacity][kTraceFields] (ACS_FLAG_TRACE)
+    StreamCtl *sctl;          // [n_streams]
     HostStatus *hstatus;      // mapped host memory
     unsigned long long timeout_ns;
     uint32_t cap_log2;        // capacity = 1 << cap_log2
@@ -120,7 +132,8 @@ struct KParams {
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses
     uint32_t poll_ns;         // longest sleep of an idle worker between ring polls
     uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
-    uint32_t end[ACS_MAX_STREAMS];    // one past the last seq of this launch
+    uint32_t end[ACS_MAX_STREAMS];    // one past the last seq submitted by the host
+    uint8_t open[ACS_MAX_STREAMS];    // emit tasks among the stream's new tasks
 };
 
 // descriptors kept in a scheduler's shared-memory history ring: the W - 1
@@ -142,7 +155,7 @@ enum SlotState : uint32_t { kEmpty = 0, kPending = 1, kReady = 2, kExec = 3, kRe
 
 // error-site codes stored in DevCtl::err_info
 enum ErrSite : uint32_t {
-    kSiteSched = 1, kSiteWorker = 2, kSiteRing = 3, kSitePrefetch = 4,
+    kSiteSched = 1, kSiteWorker = 2, kSiteRing = 3, kSitePrefetch = 4, kSiteEmit = 8,
     // self-checks (ACS_ERR_INVALID): a descriptor or work unit that is not what it must be
     kSiteCheckRecord = 5, kSiteWorkerPayload = 6, kSiteWorkerRecord = 7
 };

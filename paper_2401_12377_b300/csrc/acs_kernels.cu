@@ -86,8 +86,8 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 struct SchedShared {
     uint32_t complete_upto;  // hist holds every seq below (loaded), from `lo`
     uint32_t next;           // tasks below are inserted
-    uint32_t quit;           // 1: checkers leave
-    uint32_t pad;
+    uint32_t quit;           // 1: checkers and loader leave
+    uint32_t end;            // stream end known to the CTA (grows while the stream is open)
 };
 
 struct DispatchEntry {
@@ -151,17 +151,48 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     const uint32_t C = 1u << P.cap_log2;
-    const uint32_t first = P.first[stream], end = P.end[stream];
+    const uint32_t first = P.first[stream];
+    uint32_t end = P.end[stream];
+    const bool open = P.open[stream] != 0;
     const TaskRec *recs = P.recs + (size_t)stream * C;
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;
     uint32_t load_upto = first > W - 1 ? first - (W - 1) : 0u;
     unsigned long long tw = 0;
     uint32_t spins = 0, backoff = 32;
-    while (load_upto < end) {
-        const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
-        const uint32_t nx = lds_volatile(&S.sh->next);
-        if (bhi + W > nx + H + 1) {
+    while (true) {
+        bool wait = false;
+        if (load_upto >= end) {
+            if (!open) return;                     // a closed stream is fully loaded
+            // an open stream grows when an emitter publishes a larger end
+            const uint32_t e = ld_relaxed_u32(&P.sctl[stream].end);
+            if ((int32_t)(e - end) > 0) {
+                fence_acq_rel_gpu();               // the emitter's descriptors are visible
+                __syncwarp();
+                end = e;
+                if (lane == 0) sts_volatile(&S.sh->end, end);
+                continue;
+            }
+            wait = true;
+        } else {
+            const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
+            const uint32_t nx = lds_volatile(&S.sh->next);
+            if (bhi + W > nx + H + 1) {
+                wait = true;
+            } else {
+                tw = 0;
+                backoff = 32;
+                const uint32_t n16 = (bhi - load_upto) * (uint32_t)(sizeof(TaskRec) / 16);
+                const uint4 *src = reinterpret_cast<const uint4 *>(recs + (load_upto & (C - 1)));
+                uint4 *dst = reinterpret_cast<uint4 *>(&S.hist[load_upto & HM]);
+                for (uint32_t i = lane; i < n16; i += 32) dst[i] = __ldcg(src + i);
+                __syncwarp();
+                __threadfence_block();
+                load_upto = bhi;
+                if (lane == 0) sts_volatile(&S.sh->complete_upto, load_upto);
+            }
+        }
+        if (wait) {
             if (lds_volatile(&S.sh->quit)) return;
             if ((++spins & 63) == 0) {
                 const unsigned long long now = globaltimer_ns();
@@ -173,18 +204,7 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
             }
             __nanosleep(backoff);
             if (backoff < 256) backoff <<= 1;
-            continue;
         }
-        tw = 0;
-        backoff = 32;
-        const uint32_t n16 = (bhi - load_upto) * (uint32_t)(sizeof(TaskRec) / 16);
-        const uint4 *src = reinterpret_cast<const uint4 *>(recs + (load_upto & (C - 1)));
-        uint4 *dst = reinterpret_cast<uint4 *>(&S.hist[load_upto & HM]);
-        for (uint32_t i = lane; i < n16; i += 32) dst[i] = __ldcg(src + i);
-        __syncwarp();
-        __threadfence_block();
-        load_upto = bhi;
-        if (lane == 0) sts_volatile(&S.sh->complete_upto, load_upto);
     }
 }
 
@@ -192,18 +212,23 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     const uint32_t first = P.first[stream], end = P.end[stream];
+    const bool open = P.open[stream] != 0;         // then tasks beyond `end` may still come
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
     constexpr uint32_t kCheckers = kBlock / 32 - 2;   // warps 1 .. 6
     unsigned long long tw = 0;
-    for (uint32_t j = first + w; j < end; j += kCheckers) {
+    unsigned long long seg_bytes = 0;
+    for (uint32_t j = first + w; open || j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
         uint32_t spins = 0, backoff = 32;
         while (true) {
             const uint32_t cu = lds_volatile(&S.sh->complete_upto);
             const uint32_t nx = lds_volatile(&S.sh->next);
             if (cu > j && j < nx + H) break;
-            if (lds_volatile(&S.sh->quit)) return;
+            if (lds_volatile(&S.sh->quit)) {
+                if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
+                return;
+            }
             if ((++spins & 63) == 0) {
                 const unsigned long long now = globaltimer_ns();
                 if (tw == 0) tw = now;
@@ -214,6 +239,11 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             }
             __nanosleep(backoff);
             if (backoff < 256) backoff <<= 1;
+        }
+        if (lane == 0) {   // algorithmic bytes: what the task's segments name
+            const TaskRec &rr = S.hist[j & HM];
+            for (uint32_t k = 0; k < rr.nseg && k < (uint32_t)kMaxSegs; ++k)
+                if (!(rr.seg[k].start == 0 && rr.seg[k].last == ~0ull)) seg_bytes += rr.seg[k].last - rr.seg[k].start + 1;
         }
         tw = 0;
         __threadfence_block();
@@ -246,6 +276,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         }
         __syncwarp();
     }
+    if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
 }
 
 // Shared-memory set-up of a scheduler CTA, before its warps take their roles
@@ -259,6 +290,14 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
         S.sh->next = first;
         S.sh->quit = 0;
+        S.sh->end = P.end[stream];
+        if (P.open[stream]) {   // published before any emitter of this launch can run
+            StreamCtl *sc = &P.sctl[stream];
+            sc->end = P.end[stream];
+            sc->open = P.open[stream];
+            sc->head_pub = first;
+            __threadfence();
+        }
     }
 }
 
@@ -266,7 +305,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     const uint32_t C = 1u << P.cap_log2;
-    const uint32_t first = P.first[stream], end = P.end[stream];
+    const uint32_t first = P.first[stream];
+    const bool open = P.open[stream] != 0;
+    uint32_t end = P.end[stream];              // grows while the stream is open
     uint32_t *done = P.done + stream * kMaxWindow;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
@@ -297,10 +338,12 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     unsigned long long tp = 0;
 #define ACS_PHASE(k) do { const unsigned long long _t = clock64(); ph[k] += _t - tp; tp = _t; } while (0)
 
-    while (first < end) {
+    uint32_t head_pub = first;
+    while (first < end || open) {
         bool progress = false;
         const unsigned long long t0 = clock64();
         tp = t0;
+        if (open) end = lds_volatile(&S.sh->end);
 
         ACS_PHASE(0);
         // 1. how many tasks are checked and have a free slot (at most 32 per
@@ -411,7 +454,20 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             if (hslot >= W) hslot -= W;
         }
         ACS_PHASE(2);
-        if (head == end) { busy += clock64() - t0; break; }
+        if (open && head != head_pub && lane == 0) {   // emitters wait on it for ring space
+            st_relaxed_u32(&P.sctl[stream].head_pub, head);
+        }
+        head_pub = head;
+        if (head == end) {
+            if (!open) { busy += clock64() - t0; break; }
+            // open stream: finished once no emitter is left and nothing was appended
+            uint32_t fin = 0;
+            if (lane == 0 && ld_relaxed_u32(&P.sctl[stream].open) == 0) {
+                fence_acq_rel_gpu();
+                fin = ld_relaxed_u32(&P.sctl[stream].end) == end;
+            }
+            if (__shfl_sync(0xffffffffu, fin, 0)) { busy += clock64() - t0; break; }
+        }
 
         // 5. dispatch, oldest first, at most 32 undispatched tasks whose active
         //    upstream tasks are all dispatched (or in this batch). A task still
@@ -583,6 +639,161 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     }
 }
 
+// ---- device-side emission (rigid-sphere stream) -----------------------------------
+
+struct EmitSmem {
+    acs_rl_emit_cfg cfg;
+    uint32_t base, n_solve, ok, pad;
+    int wcnt[kBlock / 32];
+    uint16_t env[1024];        // environments with islands, ascending
+    uint8_t nisl[1024];
+};
+
+static_assert(sizeof(EmitSmem) <= kBodySmem, "emit smem");
+
+// One descriptor written straight into the stream's device ring: header, args
+// and the segments acs_get_addresses derives for the same args.
+__device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, uint16_t ncta, const void *args,
+                                        uint32_t args_bytes, const Seg *segs, uint32_t nseg, uint16_t wmask) {
+    TaskHdr h;
+    uint32_t *hw = reinterpret_cast<uint32_t *>(&h);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hw[i] = 0;
+    h.task_id = seq;
+    h.op = op;
+    h.ncta = ncta;
+    h.wmask = wmask;
+    h.nseg = (uint8_t)nseg;
+    h.seq = seq;
+    const uint32_t *aw = reinterpret_cast<const uint32_t *>(args);
+    for (uint32_t i = 0; i < args_bytes / 4; ++i) hw[4 + i] = aw[i];
+    uint4 *dst = reinterpret_cast<uint4 *>(r);
+    const uint4 *src = reinterpret_cast<const uint4 *>(&h);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dst[i] = src[i];
+    for (uint32_t k = 0; k < nseg; ++k) r->seg[k] = segs[k];
+}
+
+__device__ __forceinline__ Seg seg_of(uint64_t a, uint64_t n) { return Seg{a, a + n - 1}; }
+
+// The emit task of step t (one CTA): appends solves, integrates, the next
+// broadphase and the next emit task after the current end of its stream, then
+// publishes the new end with release semantics.
+__device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &hdr, uint8_t *smem) {
+    EmitSmem &E = *reinterpret_cast<EmitSmem *>(smem);
+    const acs_rl_emit_args a = load_args<acs_rl_emit_args>(hdr.args);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t C = 1u << P.cap_log2, W = P.window;
+    StreamCtl *sc = &P.sctl[stream];
+    TaskRec *ring = P.recs + (size_t)stream * C;
+    const uint32_t n_env = a.n_env, chunk = a.chunk, n_chunks = a.n_env / a.chunk;
+    const bool more = a.step + 1 < a.steps;
+    if (tid < sizeof(acs_rl_emit_cfg) / 4)
+        reinterpret_cast<uint32_t *>(&E.cfg)[tid] = reinterpret_cast<const uint32_t *>(a.cfg)[tid];
+    if (tid == 0) E.ok = n_env <= 1024 && chunk > 0 && n_env % chunk == 0;
+    __syncthreads();
+    if (!E.ok) {
+        if (tid == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteEmit);
+        return;
+    }
+    // environments with islands, in ascending order (ballot scan per 256)
+    const uint32_t *nisl = reinterpret_cast<const uint32_t *>(a.nisl);
+    uint32_t count = 0;
+    for (uint32_t e0 = 0; e0 < n_env; e0 += kBlock) {
+        const uint32_t e = e0 + tid;
+        const uint32_t k = e < n_env ? nisl[e] : 0u;
+        const bool has = k > 0;
+        const uint32_t bal = __ballot_sync(0xffffffffu, has);
+        if (lane == 0) E.wcnt[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t off = count;
+        for (uint32_t w = 0; w < warp; ++w) off += E.wcnt[w];
+        if (has) {
+            const uint32_t pos = off + __popc(bal & ((1u << lane) - 1u));
+            E.env[pos] = (uint16_t)e;
+            E.nisl[pos] = (uint8_t)min(k, 255u);
+        }
+        for (uint32_t w = 0; w < kBlock / 32; ++w) count += E.wcnt[w];
+        __syncthreads();
+    }
+    const uint32_t n_solve = count;
+    const uint32_t n_new = n_solve + n_chunks + (more ? n_chunks + 1 : 0);
+    // position of the first new task; wait (bounded) until the ring positions
+    // it overwrites hold only released tasks no window still looks at
+    if (tid == 0) {
+        const uint32_t base = ld_relaxed_u32(&sc->end);
+        unsigned long long tw = 0;
+        uint32_t ok = 1;
+        while ((int32_t)(base + n_new + W - (ld_relaxed_u32(&sc->head_pub) + C)) > 0) {
+            if (stopped(P)) { ok = 0; break; }
+            const unsigned long long now = globaltimer_ns();
+            if (tw == 0) tw = now;
+            else if (now - tw > P.timeout_ns) {
+                raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteEmit);
+                ok = 0;
+                break;
+            }
+            __nanosleep(256);
+        }
+        E.base = base;
+        E.ok = ok;
+    }
+    __syncthreads();
+    if (!E.ok) return;
+    const uint32_t base = E.base;
+    const acs_rl_emit_cfg &cfg = E.cfg;
+    const uint8_t *table = reinterpret_cast<const uint8_t *>(a.ncta_table);
+    constexpr uint64_t kPos = 32 * 3 * 4, kProp = 32 * 2 * 4, kRec = ACS_RL_REC_BYTES;
+    for (uint32_t k = tid; k < n_new; k += kBlock) {
+        const uint32_t seq = base + k;
+        TaskRec *r = ring + (seq & (C - 1));
+        Seg sg[5];
+        if (k < n_solve) {
+            const uint64_t e = E.env[k];
+            acs_rl_solve_args x{cfg.pos + e * kPos, cfg.prop + e * kProp, cfg.cont + e * kRec, cfg.vel + e * kPos,
+                                cfg.beta_dt, cfg.slop};
+            sg[0] = seg_of(x.pos, kPos); sg[1] = seg_of(x.prop, kProp); sg[2] = seg_of(x.cont, kRec);
+            sg[3] = seg_of(x.vel, kPos); sg[4] = seg_of(x.vel, kPos);
+            const uint16_t nc = (uint16_t)min(max((uint32_t)E.nisl[k], 1u), 16u);
+            put_rec(r, seq, ACS_OP_RL_SOLVE, nc, &x, sizeof x, sg, 5, 1u << 4);
+        } else if (k < n_solve + n_chunks) {
+            const uint64_t c = k - n_solve, e0 = c * chunk;
+            acs_rl_integrate_args x{cfg.pos + e0 * kPos, cfg.vel + e0 * kPos, cfg.prop + e0 * kProp, chunk,
+                                    cfg.dt, cfg.gdt, cfg.box};
+            sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.vel, chunk * kPos); sg[2] = seg_of(x.prop, chunk * kProp);
+            sg[3] = seg_of(x.pos, chunk * kPos); sg[4] = seg_of(x.vel, chunk * kPos);
+            const uint16_t nc = table[(a.step * 2 + 1) * n_chunks + c];
+            put_rec(r, seq, ACS_OP_RL_INTEGRATE, nc, &x, sizeof x, sg, 5, (1u << 3) | (1u << 4));
+        } else if (k < n_solve + 2 * n_chunks) {
+            const uint64_t c = k - n_solve - n_chunks, e0 = c * chunk;
+            acs_rl_broadphase_args x{cfg.pos + e0 * kPos, cfg.prop + e0 * kProp, cfg.cont + e0 * kRec,
+                                     a.nisl + e0 * 4, chunk, 0};
+            sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.prop, chunk * kProp);
+            sg[2] = seg_of(x.cont, chunk * kRec); sg[3] = seg_of(x.nisl, chunk * 4);
+            const uint16_t nc = table[((a.step + 1) * 2 + 0) * n_chunks + c];
+            put_rec(r, seq, ACS_OP_RL_BROADPHASE, nc, &x, sizeof x, sg, 4, (1u << 2) | (1u << 3));
+        } else {
+            acs_rl_emit_args x = a;
+            x.step = a.step + 1;
+            sg[0] = seg_of(x.nisl, (uint64_t)n_env * 4);
+            sg[1] = seg_of(x.cfg, sizeof(acs_rl_emit_cfg));
+            sg[2] = seg_of(x.ncta_table, (uint64_t)(x.steps + 1) * 2 * n_chunks);
+            sg[3] = seg_of(x.token, 4);
+            put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();                       // descriptors before the new end
+        st_release_u32(&sc->end, base + n_new);
+        atomicAdd(&P.sched_stats[stream].emitted, (unsigned long long)n_new);
+        if (!more) {
+            __threadfence();                   // the final end before the stream closes
+            atomicSub(&sc->open, 1u);
+        }
+    }
+}
+
 // ---- worker CTAs ----------------------------------------------------------------
 
 __device__ void worker_loop(const KParams &P, uint8_t *smem) {
@@ -681,7 +892,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             const unsigned long long t = atomicAdd(&P.ctl->ticket, 1ull);
             atomicMin(&P.log_start[((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))], t);
         }
-        run_body(s_hdr, (int)cta, smem, &P.ctl->stop);
+        if (s_hdr.op == ACS_OP_RL_EMIT) body_rl_emit(P, stream, s_hdr, smem);
+        else run_body(s_hdr, (int)cta, smem, &P.ctl->stop);
         __syncthreads();
         if (threadIdx.x == 0) {
             bool last = true;

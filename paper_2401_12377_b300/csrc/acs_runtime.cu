@@ -35,6 +35,8 @@ struct StreamState {
     uint32_t synced = 0;     // seqs below are known retired (last acs_sync)
     bool has_id = false;
     uint32_t last_id = 0;
+    uint32_t emit_pending = 0;  // emit tasks submitted since the last flush
+    bool emitting = false;      // flushed emit tasks not yet synced: the device owns the end
 };
 
 struct TimedLaunch {
@@ -65,6 +67,7 @@ struct acs_ctx {
     unsigned long long *d_log_mask = nullptr, *d_log_start = nullptr, *d_log_retire = nullptr;
     SchedStats *d_sched_stats = nullptr;
     unsigned long long *d_trace = nullptr;
+    StreamCtl *d_sctl = nullptr;
     HostStatus *h_status = nullptr, *d_status = nullptr;
     std::vector<StreamState> st;
     int err = ACS_OK;
@@ -131,7 +134,7 @@ bool valid_op(uint16_t op) {
     switch (op) {
     case ACS_OP_NOP: case ACS_OP_AXPY: case ACS_OP_SCALE: case ACS_OP_ADD: case ACS_OP_GEMV:
     case ACS_OP_BIAS_RELU: case ACS_OP_RESID: case ACS_OP_RL_BROADPHASE: case ACS_OP_RL_SOLVE:
-    case ACS_OP_RL_INTEGRATE: case ACS_OP_WAIT_FLAG: case ACS_OP_SLEEP:
+    case ACS_OP_RL_INTEGRATE: case ACS_OP_RL_EMIT: case ACS_OP_WAIT_FLAG: case ACS_OP_SLEEP:
         return true;
     default:
         return false;
@@ -193,6 +196,7 @@ int flush_window(acs_ctx *c) {
     P.log_retire = c->d_log_retire;
     P.sched_stats = c->d_sched_stats;
     P.trace = c->d_trace;
+    P.sctl = c->d_sctl;
     P.hstatus = c->d_status;
     P.timeout_ns = c->cfg.timeout_ns;
     P.cap_log2 = c->cap_log2;
@@ -206,6 +210,7 @@ int flush_window(acs_ctx *c) {
     for (uint32_t s = 0; s < c->S; ++s) {
         P.first[s] = c->st[s].flushed;
         P.end[s] = c->st[s].submitted;
+        P.open[s] = (uint8_t)std::min<uint32_t>(c->st[s].emit_pending, 255u);
     }
     void *args[] = {&P};
     TimedLaunch t{};
@@ -401,6 +406,7 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_log_retire);
     cudaFree(c->d_sched_stats);
     cudaFree(c->d_trace);
+    cudaFree(c->d_sctl);
     if (c->h_ring) cudaFreeHost(c->h_ring);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -479,11 +485,13 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMalloc(&c->d_log_start, nlog * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_log_retire, nlog * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_sched_stats, c->S * sizeof(SchedStats)));
+    chk(cudaMalloc(&c->d_sctl, c->S * sizeof(StreamCtl)));
     chk(cudaHostAlloc(&c->h_status, sizeof(HostStatus), cudaHostAllocMapped));
     if (rc) { acs_destroy(c); return rc; }
     std::memset((void *)c->h_status, 0, sizeof(HostStatus));
     chk(cudaHostGetDevicePointer((void **)&c->d_status, (void *)c->h_status, 0));
     chk(cudaMemsetAsync(c->d_sched_stats, 0, c->S * sizeof(SchedStats), c->stream));
+    chk(cudaMemsetAsync(c->d_sctl, 0, c->S * sizeof(StreamCtl), c->stream));
     chk(cudaMemsetAsync(c->d_log_mask, 0, nlog * sizeof(unsigned long long), c->stream));
     chk(launch_init(c->d_cells, c->ncells, c->d_ctl, c->d_done, c->d_remaining, nslots, c->stream));
 
@@ -572,6 +580,13 @@ int acs_get_addresses(const acs_args *a, acs_segment *r, uint32_t *nr, acs_segme
         wr(x.pos, x.nenv * S * 3 * F); wr(x.vel, x.nenv * S * 3 * F);
         break;
     }
+    case ACS_OP_RL_EMIT: {  // reads nisl, the cfg block and the CTA table; writes the token
+        acs_rl_emit_args x; std::memcpy(&x, a->bytes, sizeof x);
+        if (!x.chunk || x.n_env % x.chunk) return ACS_ERR_INVALID;
+        rd(x.nisl, (uint64_t)x.n_env * F); rd(x.cfg, sizeof(acs_rl_emit_cfg));
+        rd(x.ncta_table, (uint64_t)(x.steps + 1) * 2 * (x.n_env / x.chunk)); wr(x.token, F);
+        break;
+    }
     case ACS_OP_WAIT_FLAG: {
         acs_wait_args x; std::memcpy(&x, a->bytes, sizeof x);
         rd(x.flag, 4);
@@ -597,6 +612,8 @@ int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_a
     if (!args || stream >= c->S || (n_reads && !reads) || (n_writes && !writes)) return ACS_ERR_INVALID;
     if (!valid_op(args->op) || args->ncta < 1 || args->ncta > ACS_MAX_NCTA || args->reserved) return ACS_ERR_INVALID;
     StreamState &ss = c->st[stream];
+    if (ss.emitting) return ACS_ERR_INVALID;   // sync first: the device appends to this stream
+    if (args->op == ACS_OP_RL_EMIT && c->cfg.mode != ACS_MODE_WINDOW) return ACS_ERR_INVALID;
     if (ss.has_id && task_id <= ss.last_id) return ACS_ERR_ORDER;
     if ((uint64_t)ss.submitted + c->W - 1 - ss.synced + 1 > c->C - kPrefetch) return ACS_ERR_FULL;
     TaskRec &r = c->h_ring[(size_t)stream * c->C + (ss.submitted & (c->C - 1))];
@@ -617,6 +634,7 @@ int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_a
     ss.has_id = true;
     ss.last_id = task_id;
     ss.submitted++;
+    if (args->op == ACS_OP_RL_EMIT) ss.emit_pending++;
     c->stats.tasks_submitted++;
     c->stats.seg_bytes += bytes;
     return ACS_OK;
@@ -656,6 +674,8 @@ int acs_flush(acs_ctx *c) {
     for (auto &s : c->st) {
         c->stats.tasks_flushed += s.submitted - s.flushed;
         s.flushed = s.submitted;
+        if (s.emit_pending) s.emitting = true;
+        s.emit_pending = 0;
     }
     return ACS_OK;
 }
@@ -671,6 +691,22 @@ int acs_sync(acs_ctx *c) {
     }
     if (c->cfg.mode == ACS_MODE_GRAPH) release_graphs(c, true);
     if (c->err) return c->err;
+    bool any = false;
+    for (auto &s : c->st) any |= s.emitting;
+    if (any) {   // the device appended tasks: continue the streams after them
+        std::vector<StreamCtl> sc(c->S);
+        e = cudaMemcpy(sc.data(), c->d_sctl, c->S * sizeof(StreamCtl), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        for (uint32_t i = 0; i < c->S; ++i) {
+            StreamState &s = c->st[i];
+            if (!s.emitting) continue;
+            const uint32_t added = sc[i].end - s.flushed;
+            c->stats.tasks_emitted += added;
+            s.submitted = s.flushed = sc[i].end;
+            if (sc[i].end) { s.has_id = true; s.last_id = std::max(s.last_id, sc[i].end - 1); }
+            s.emitting = false;
+        }
+    }
     for (auto &s : c->st) s.synced = s.flushed;
     return ACS_OK;
 }
@@ -742,8 +778,10 @@ int acs_get_stats(acs_ctx *c, acs_stats *out) {
         if (cudaMemcpy(ss.data(), c->d_sched_stats, c->S * sizeof(SchedStats), cudaMemcpyDeviceToHost) == cudaSuccess) {
             c->stats.sched_cycles = c->stats.sched_busy_cycles = c->stats.sched_inserts = 0;
             c->stats.sched_iterations = 0;
+            c->stats.device_seg_bytes = 0;
             for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] = 0;
             for (auto &x : ss) {
+                c->stats.device_seg_bytes += x.seg_bytes;
                 for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] += x.phase[k];
                 c->stats.sched_cycles += x.cycles;
                 c->stats.sched_busy_cycles += x.busy_cycles;

@@ -32,6 +32,8 @@ OP_DTYPES = {
                           ("slop", "<f4")]),
     "rl_integrate": np.dtype([("pos", _U8), ("vel", _U8), ("prop", _U8), ("nenv", "<u4"), ("dt", "<f4"),
                               ("gdt", "<f4"), ("box", "<f4")]),
+    "rl_emit": np.dtype([("cfg", _U8), ("nisl", _U8), ("token", _U8), ("ncta_table", _U8), ("n_env", "<u4"),
+                         ("step", "<u4"), ("steps", "<u4"), ("chunk", "<u4")]),
     "wait_flag": np.dtype([("flag", _U8), ("limit_ns", _U8)]),
     "sleep": np.dtype([("y", _U8), ("ns", _U8), ("tag", "<f4"), ("pad", "<u4")]),
 }
@@ -98,6 +100,10 @@ def pack_task(task, bufs: DeviceBuffers) -> np.ndarray:
              "nenv": S["nenv"], "dt": S["dt"], "gdt": S["gdt"], "box": S["box"]}
     elif op == "sleep":
         f = {"y": bufs.ptr(A["y"]), "ns": S["ns"], "tag": S["tag"]}
+    elif op == "rl_emit":
+        f = {"cfg": S["cfg"], "nisl": bufs.ptr(A["nisl"]), "token": bufs.ptr(A["token"]),
+             "ncta_table": S["ncta_table"], "n_env": A["nisl"].n, "step": S["step"], "steps": S["steps"],
+             "chunk": S["chunk"]}
     elif op == "wait_flag":
         f = {"flag": S["flag"], "limit_ns": S["limit_ns"]}
     else:
@@ -261,6 +267,52 @@ class RLDriver:
             if record_plans:
                 plans.append(plan)
         return plans
+
+
+EMIT_CFG_DTYPE = np.dtype([("pos", _U8), ("vel", _U8), ("prop", _U8), ("cont", _U8), ("beta_dt", "<f4"),
+                           ("slop", "<f4"), ("dt", "<f4"), ("gdt", "<f4"), ("box", "<f4"), ("pad", "<u4", 3)])
+assert EMIT_CFG_DTYPE.itemsize == 64
+
+
+class RLEmitDriver:
+    """Runs a streamgen.RLSim on the GPU with device-side emission: the host
+    submits the first broadphase batch and the first emit task once; every
+    later task is appended on the device by emit tasks, so the whole run is one
+    flush, one persistent launch and one sync."""
+
+    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context):
+        self.sim, self.bufs, self.ctx = sim, bufs, ctx
+        p = sim.p
+        sc = sim.scalars()
+        cfg = np.zeros(1, EMIT_CFG_DTYPE)
+        for k in ("pos", "vel", "prop", "cont"):
+            cfg[k] = bufs.base[k]
+        for k in ("beta_dt", "slop"):
+            cfg[k] = sc["rl_solve"][k]
+        for k in ("dt", "gdt", "box"):
+            cfg[k] = sc["rl_integrate"][k]
+        self.cfg = torch.from_numpy(cfg.view(np.uint8).copy()).to("cuda")
+        self.table = torch.from_numpy(sim.ncta_table()).to("cuda")
+
+    def first_tasks(self):
+        p = self.sim.p
+        tasks = self.sim.first_batch()
+        if p.steps > 0:
+            e = self.sim.emit_task(0)
+            e.scalars.update({"cfg": int(self.cfg.data_ptr()), "ncta_table": int(self.table.data_ptr()),
+                              "steps": np.uint32(p.steps), "chunk": np.uint32(p.chunk)})
+            tasks.append(e)
+        return tasks
+
+    def run(self) -> int:
+        """One complete run; returns the number of tasks the stream had."""
+        before = self.ctx.stats()
+        tasks = self.first_tasks()
+        self.ctx.submit(tasks, self.bufs)
+        self.ctx.flush()
+        self.ctx.sync()
+        after = self.ctx.stats()
+        return (after["tasks_flushed"] - before["tasks_flushed"]) + (after["tasks_emitted"] - before["tasks_emitted"])
 
 
 def _one_plan(kind: int, idx: int):

@@ -219,7 +219,14 @@ class RLSim:
         self.next_id = 0
 
     # -- initial state -------------------------------------------------------
-    def buffers(self) -> Dict[str, np.ndarray]:
+    def buffers(self, emit: bool = False) -> Dict[str, np.ndarray]:
+        """Initial state; with ``emit`` also the emit tasks' 4-byte token."""
+        b = self._buffers()
+        if emit:
+            b["token"] = np.zeros(1, np.uint32)
+        return b
+
+    def _buffers(self) -> Dict[str, np.ndarray]:
         p, S = self.p, RL_SPHERES
         rng = np.random.default_rng(self.seed)
         radius = rng.uniform(0.05, 0.1, (p.n_env, S)).astype(np.float32)
@@ -314,6 +321,32 @@ class RLSim:
                     out.append(Task(int(tid), "rl_integrate", int(nc), {"pos": pos, "vel": vel, "prop": prop},
                                     dict(sc["rl_integrate"])))
         return out
+
+    # -- device-side emission ------------------------------------------------------
+    # In the emitting variant of the stream an ``rl_emit`` task follows each
+    # broadphase batch: it reads the island counts and appends the next batch
+    # (the same tasks ``step_plan`` lists) followed by the next emit task.
+    # Program order: bp(0), emit(0), [solves(0), int(0), bp(1), emit(1)], ...,
+    # [solves(T-1), int(T-1)].
+
+    def ncta_table(self) -> np.ndarray:
+        """CTA counts of chunk tasks: entry ((t * 2 + k) * n_chunks + c) is the
+        broadphase (k = 0) or integrate (k = 1) CTA count of chunk c, step t."""
+        nch = self.p.n_env // self.p.chunk
+        tab = np.zeros((self.p.steps + 1, 2, nch), np.uint8)
+        for t in range(self.p.steps + 1):
+            for k in range(2):
+                for c in range(nch):
+                    tab[t, k, c] = self._chunk_ncta(k, t, c)
+        return tab.reshape(-1)
+
+    def emit_task(self, step: int) -> Task:
+        """The emit task that follows the broadphase of ``step``."""
+        t = Task(self.next_id, "rl_emit", 1,
+                 {"nisl": Ref("nisl", 0, self.p.n_env), "token": Ref("token", 0, 1)},
+                 {"step": np.uint32(step)})
+        self.next_id += 1
+        return t
 
     # -- batches ---------------------------------------------------------------------
     def first_batch(self) -> List[Task]:

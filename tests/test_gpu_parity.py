@@ -188,3 +188,57 @@ def test_rlsim_small_parity(seed, n_env, steps):
     assert [(t.op, t.ncta, t.arrays) for t in g_tasks] == [(t.op, t.ncta, t.arrays) for t in o_tasks]
     check_log(masks, start, retire, E, D, sim.window)
     assert_same(out, o_bufs, "rl GPU vs oracle")
+
+
+# ---- device-side emission: the whole rigid-sphere run in one launch -------------------
+
+def _rl_emit_gpu(seed, params, log=True):
+    sim = sg.RLSim(seed, params)
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    with harness.Context(sim.window, log=log, capacity=1 << 14) as ctx:
+        drv = harness.RLEmitDriver(sim, bufs, ctx)
+        n = drv.run()
+        lg = ctx.log(0, 0, n) if log else None
+        st = ctx.stats()
+    return n, bufs.download(), lg, st
+
+
+@pytest.mark.parametrize("seed,n_env,steps", [(1, 16, 6), (4, 64, 5), (5, 256, 4)])
+def test_rlsim_device_emission_small(seed, n_env, steps):
+    p = sg.RLParams(n_env=n_env, steps=steps)
+    n, out, (masks, start, retire), st = _rl_emit_gpu(seed, p)
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(seed, sg.RLParams(n_env=n_env, steps=steps)), emit=True)
+    assert n == len(o_tasks)                                  # same input-dependent stream length
+    assert st["launches"] == 1 and st["tasks_emitted"] == n - st["tasks_flushed"]
+    segs = addresses.stream_segments(o_tasks, o_bufs)
+    E = deps.full_dag(segs)
+    check_log(masks, start, retire, E, deps.window_dag(E, 32), 32)
+    assert_same(out, o_bufs, "device emission vs oracle")
+
+
+def test_rlsim_device_emission_full_size():
+    """256 envs x 32 spheres x 50 steps (~15 000 tasks) in one launch: the
+    window DAG and outputs equal the oracle's; legality is checked on D_W
+    plus in-order release (which covers every longer edge of E)."""
+    n, out, (masks, start, retire), st = _rl_emit_gpu(1, sg.RLParams())
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(1, sg.RLParams()), emit=True)
+    assert n == len(o_tasks)
+    segs = addresses.stream_segments(o_tasks, o_bufs)
+    D = deps.window_dag_direct(segs, 32)
+    assert deps.edges_from_masks([int(m) for m in masks], 32) == D
+    s_, r_ = [int(x) for x in start], [int(x) for x in retire]
+    assert not deps.check_legal(D, s_, r_)
+    assert not deps.check_release_order(s_, r_, 32)
+    assert_same(out, o_bufs, "device emission vs oracle, full size")
+
+
+def test_rlsim_device_emission_matches_host_driven_outputs():
+    p = sg.RLParams(n_env=64, steps=8)
+    _, out_emit, _, _ = _rl_emit_gpu(7, p, log=False)
+    sim = sg.RLSim(7, sg.RLParams(n_env=64, steps=8))
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    with harness.Context(32, capacity=1 << 14) as ctx:
+        harness.RLDriver(sim, bufs, ctx).run()
+    out_host = bufs.download()
+    for k in ("pos", "vel", "cont", "nisl"):
+        assert np.array_equal(out_emit[k], out_host[k]), k

@@ -233,3 +233,22 @@ def test_ring_window_issue_is_legal_and_schedule_independent(seed):
         out = execute.run_inorder(s.buffers, s.tasks, order)
         for k in ref:
             assert np.array_equal(ref[k], out[k])
+
+
+def test_window_dag_direct_equals_window_of_E():
+    for seed in range(4):
+        s = sg.elementwise_stream(seed, n_tasks=70, ranges=True)
+        segs = addresses.stream_segments(s.tasks, s.buffers)
+        E = deps.full_dag(segs)
+        for W in (1, 2, 8, 33):
+            assert deps.window_dag_direct(segs, W) == deps.window_dag(E, W)
+
+
+def test_release_order_check_accepts_ring_issue_and_rejects_a_violation():
+    s = sg.elementwise_stream(8, n_tasks=48)
+    E = deps.full_dag(addresses.stream_segments(s.tasks, s.buffers))
+    start, retire = _simulate_ring_window(len(s.tasks), E, 8, random.Random(0))
+    assert deps.check_release_order(start, retire, 8) == []
+    bad = list(start)
+    bad[20] = -1                                # starts before anything retired
+    assert deps.check_release_order(bad, retire, 8)
