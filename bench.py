@@ -3,13 +3,19 @@
 
 One bench step = one complete run of the stream: 256 environments x 32 spheres,
 50 simulation steps, window 32, about 300 small tasks (1-16 CTAs) per
-simulation step whose task graph depends on the simulated contacts. Per
-simulation step the host submits one batch through the C ABI, flushes, syncs
-and reads back the island counts (1 KiB) the broadphase tasks wrote, which
-decide the next batch's tasks.
+simulation step whose task graph depends on the simulated contacts (island
+counts the broadphase tasks compute decide the next step's tasks).
+
+The method runs it with device-side emission: the host submits the first
+broadphase batch and an emit task once; emit tasks append each next step's
+tasks on the device; one flush, one persistent launch, one sync per run. The
+host-driven arm runs the same scheduler with one flush per simulation step
+(the host reads back the 1 KiB of island counts and submits the next batch),
+as do the in-order and CUDA-graph arms, which cannot emit on the device.
 
 Prints ONE JSON line (rank 0). Arms measured on the same box and workload:
-  value                  window scheduler (acs_flush -> persistent kernel)
+  value                  window scheduler, device-side emission
+  window_host_driven     window scheduler, one flush per simulation step
   inorder                one kernel launch per task on one stream
   graph_launch           CUDA graph of each batch's full DAG, launch time only
   graph_with_build       same, including host DAG build + instantiate
@@ -164,18 +170,19 @@ class ClockSampler:
 class RLBench:
     """One mode (window / inorder / graph) on one device state."""
 
-    def __init__(self, mode, seed, window, cta_slots, timing=True):
+    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False):
         import torch
         import streamgen as sg
         from paper_2401_12377_b300 import harness
         self.torch = torch
         self.sim = sg.RLSim(seed, rl_params())
-        host = self.sim.buffers()
+        host = self.sim.buffers(emit=emit)
         self.bufs = harness.DeviceBuffers(host)
         self.pristine = {k: v.clone() for k, v in self.bufs.t.items()}
         self.host_pinned = {k: torch.from_numpy(v.view("uint8").copy()).pin_memory() for k, v in host.items()}
         self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots)
-        self.driver = harness.RLDriver(self.sim, self.bufs, self.ctx)
+        self.emit = emit
+        self.driver = (harness.RLEmitDriver if emit else harness.RLDriver)(self.sim, self.bufs, self.ctx)
         self.mode = mode
 
     def reset_device(self):
@@ -187,7 +194,13 @@ class RLBench:
             t.copy_(self.host_pinned[k], non_blocking=True)
 
     def run_once(self, latencies=None):
-        """One full stream; returns tasks submitted."""
+        """One full stream; returns its number of tasks."""
+        if self.emit:
+            t0 = time.perf_counter()
+            n = self.driver.run()
+            if latencies is not None:
+                latencies.append(time.perf_counter() - t0)
+            return n
         before = self.ctx.stats()["tasks_submitted"]
         plan = self.sim.first_plan()
         steps = self.sim.p.steps
@@ -253,9 +266,9 @@ def time_e2e(arm, steps):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / steps
     h2d_inputs = sum(t.numel() for t in arm.host_pinned.values())
-    n_flush = arm.sim.p.steps + 1
+    n_flush = 1 if arm.emit else arm.sim.p.steps + 1
     desc_bytes = (tasks // steps) * 320
-    d2h = out_pos.numel() + out_vel.numel() + arm.sim.p.steps * arm.sim.p.n_env * 4
+    d2h = out_pos.numel() + out_vel.numel() + (0 if arm.emit else arm.sim.p.steps * arm.sim.p.n_env * 4)
     return {"value": (tasks / steps) / (ms / 1e3), "unit": "tasks/s",
             "h2d_bytes_per_step": int(h2d_inputs + desc_bytes), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": ms, "flushes_per_step": n_flush}
@@ -293,8 +306,8 @@ def main():
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     seed = 1 + rank
 
-    # ---- the method ------------------------------------------------------------------
-    acs_arm = RLBench("window", seed, args.window, args.cta_slots)
+    # ---- the method: window scheduler with device-side emission (one launch per run) ----
+    acs_arm = RLBench("window", seed, args.window, args.cta_slots, emit=True)
     latencies = []
     if dist:
         dist.barrier()
@@ -313,7 +326,7 @@ def main():
     launches = st["launches"]
     kernel_ms = st["kernel_ms"]
     avg_launch_s = (kernel_ms / 1e3) / max(1, launches)
-    bytes_per_launch = st["seg_bytes"] / max(1, launches)
+    bytes_per_launch = st["device_seg_bytes"] / max(1, launches)
     achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6400.0))
     lat_us = sorted(1e6 * x for x in latencies)
@@ -322,11 +335,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "window": args.window, "tasks_per_step": tasks_per_step,
-                       "flushes_per_step": acs_arm.sim.p.steps + 1, "cta_slots": st.get("cta_slots"),
+                       "mode": "window scheduler, device-side emission: one flush and one launch per run",
+                       "flushes_per_step": 1, "cta_slots": st.get("cta_slots"),
                        "grid": st.get("grid"), "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
-            "sim_step_latency_us": {"p50": lat_us[len(lat_us) // 2] if lat_us else None,
-                                    "p99": lat_us[min(len(lat_us) - 1, int(0.99 * len(lat_us)))] if lat_us else None},
+            "run_latency_us": {"p50": lat_us[len(lat_us) // 2] if lat_us else None,
+                               "p99": lat_us[min(len(lat_us) - 1, int(0.99 * len(lat_us)))] if lat_us else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "acs_persistent_kernel", "peak_source": peak_src,
@@ -340,6 +354,18 @@ def main():
 
     # ---- baselines on the same box -----------------------------------------------------------
     if not args.no_baselines:
+        host = RLBench("window", seed, args.window, args.cta_slots)
+        step_lat = []
+        r_h = time_arm(host, args.steps, max(1, args.warmup // 2), flush_buf, step_lat)
+        ms_h = statistics.mean(r_h["ms"])
+        tph = r_h["tasks"] / args.steps
+        sl = sorted(1e6 * x for x in step_lat)
+        line["window_host_driven"] = {
+            "tasks_per_s": tph / (ms_h / 1e3), "ms_per_step": ms_h, "flushes_per_step": host.sim.p.steps + 1,
+            "kernel_ms_per_step": r_h["stats"]["kernel_ms"] / args.steps,
+            "sim_step_latency_us": {"p50": sl[len(sl) // 2], "p99": sl[min(len(sl) - 1, int(0.99 * len(sl)))]},
+            "note": "same scheduler, host reads back island counts and submits each simulation step"}
+        host.ctx.close()
         inorder = RLBench("inorder", seed, args.window, args.cta_slots)
         r_in = time_arm(inorder, args.steps, max(1, args.warmup // 2), flush_buf)
         ms_in = statistics.mean(r_in["ms"])
@@ -348,16 +374,20 @@ def main():
         ms_g = statistics.mean(r_g["ms"])
         g_launch_ms = r_g["stats"]["kernel_ms"] / args.steps
         g_build_ms = (r_g["stats"]["graph_build_ms"] + r_g["stats"]["graph_instantiate_ms"]) / args.steps
-        line["inorder"] = {"tasks_per_s": tasks_per_step / (ms_in / 1e3), "ms_per_step": ms_in}
-        line["graph_with_build"] = {"tasks_per_s": tasks_per_step / (ms_g / 1e3), "ms_per_step": ms_g,
+        tpi = r_in["tasks"] / args.steps
+        line["inorder"] = {"tasks_per_s": tpi / (ms_in / 1e3), "ms_per_step": ms_in}
+        line["graph_with_build"] = {"tasks_per_s": tpi / (ms_g / 1e3), "ms_per_step": ms_g,
                                     "host_build_instantiate_ms_per_step": g_build_ms}
-        line["graph_launch"] = {"tasks_per_s": tasks_per_step / (g_launch_ms / 1e3),
+        line["graph_launch"] = {"tasks_per_s": tpi / (g_launch_ms / 1e3),
                                 "device_ms_per_step": g_launch_ms,
                                 "note": "sum of graph launch device times only (build excluded, "
                                         "host round trips between graphs excluded)"}
+        # per-run times compare the same simulation (the emitting stream has one
+        # emit task per step on top of the ~15 000 tasks every arm runs)
         line["speedup_vs_inorder"] = ms_in / ms_step
         line["speedup_vs_graph_with_build"] = ms_g / ms_step
         line["speedup_vs_graph_launch_only"] = g_launch_ms / ms_step
+        line["speedup_host_driven_window_vs_inorder"] = ms_in / ms_h
         line["acs_kernel_ms_per_step"] = kernel_ms / args.steps
         line["speedup_kernel_time_vs_graph_launch"] = g_launch_ms / (kernel_ms / args.steps)
         inorder.ctx.close()

@@ -195,6 +195,9 @@ typedef struct acs_stats {
                                    cell aux words, publication fence, cell stores */
     uint64_t tasks_emitted;     /* tasks appended on the device by emit tasks */
     uint64_t device_seg_bytes;  /* segment bytes of every checked task (host- or device-submitted) */
+    uint64_t check_cycles;      /* ACS_FLAG_TRACE: SM cycles the checker warps spent testing */
+    uint64_t starved_iters;     /* ACS_FLAG_TRACE: scheduler iterations with a free slot but no
+                                   checked task */
     uint32_t cta_slots;         /* worker CTAs of the persistent kernel */
     uint32_t grid;              /* total CTAs of the persistent kernel */
 } acs_stats;

@@ -66,7 +66,8 @@ class acs_stats(C.Structure):
                 ("sched_cycles", C.c_uint64), ("sched_busy_cycles", C.c_uint64),
                 ("sched_inserts", C.c_uint64), ("sched_iterations", C.c_uint64),
                 ("sched_phase_cycles", C.c_uint64 * 8), ("tasks_emitted", C.c_uint64),
-                ("device_seg_bytes", C.c_uint64), ("cta_slots", C.c_uint32),
+                ("device_seg_bytes", C.c_uint64), ("check_cycles", C.c_uint64),
+                ("starved_iters", C.c_uint64), ("cta_slots", C.c_uint32),
                 ("grid", C.c_uint32)]
 
 

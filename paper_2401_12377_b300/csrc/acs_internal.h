@@ -12,7 +12,7 @@ constexpr int kBlock = ACS_BLOCK_THREADS;
 constexpr int kMaxSegs = ACS_MAX_SEGS;
 constexpr int kMaxWindow = ACS_MAX_WINDOW;
 constexpr int kPrefetch = 16;          // descriptors per prefetch batch (bulk copy)
-constexpr int kBodySmem = 4096;        // shared memory reserved for task bodies
+constexpr int kBodySmem = 16384;       // shared memory reserved for task bodies
 constexpr uint32_t kMinCapacity = 64;
 
 // An inclusive byte range [start, last]; empty segments are never stored.
@@ -36,6 +36,15 @@ struct alignas(16) TaskRec {
     Seg seg[kMaxSegs];
 };
 static_assert(sizeof(TaskRec) == 320, "TaskRec layout");
+
+// A descriptor in a scheduler's shared-memory history, padded to 336 bytes so
+// that 16-byte segment loads of consecutive records by the lanes of a warp hit
+// distinct banks.
+struct alignas(16) HistRec {
+    TaskRec r;
+    uint4 pad;
+};
+static_assert(sizeof(HistRec) == 336, "HistRec layout");
 
 struct alignas(16) TaskHdr {   // the first 64 bytes of a TaskRec
     uint32_t task_id;
@@ -87,6 +96,8 @@ struct SchedStats {
     unsigned long long phase[kPhases];
     unsigned long long seg_bytes;   // read + write segment bytes of the checked tasks
     unsigned long long emitted;     // descriptors appended by device-side emitters
+    unsigned long long check_cycles;    // tracing: cycles checker warps spent testing
+    unsigned long long starved_iters;   // tracing: iterations with a free slot but no checked task
 };
 
 // per-task trace fields (globaltimer ns): insert, dispatch, first CTA start,
@@ -114,6 +125,7 @@ struct KParams {
     TaskRec *recs;            // [n_streams][capacity]
     DevCtl *ctl;
     unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
+                              // (descriptor index << 8 | CTA index)
     CellAux *cellaux;         // [cells]
     uint32_t *done;           // [n_streams][kMaxWindow]: seq + 1 of the slot's retired task
     uint32_t *remaining;      // [n_streams][kMaxWindow]: CTAs of the slot's task that finished
@@ -142,7 +154,7 @@ __host__ __device__ inline uint32_t hist_size(uint32_t window) { return window <
 
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    return H * (uint32_t)sizeof(TaskRec) + H * 8 + H * 4 + 16 + 32 * 24;
+    return H * 336u + H * 8 + H * 4 + 16 + 8 + kMaxWindow * 4;
 }
 
 inline uint32_t dyn_smem_bytes(uint32_t window) {

@@ -75,13 +75,17 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 //   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
 //   sh          counters shared by the warps
 //
-// Warps 1..6 ("checkers") compute pmask for tasks j = first + w + 6k: the
-// segment-overlap test of Alg. 1 (extended to RAW) of task j against its W - 1
-// predecessors, one predecessor per lane, ballot -> mask. The candidate set of
-// a task is fixed by the stream, so the test runs ahead of execution, in
-// parallel with it. Warp 7 loads descriptors. Warp 0 owns the state machine:
-// it inserts checked tasks into the W-slot ring (upstream = pmask & active
-// slots), polls completion, releases slots in program order and dispatches.
+// Warps 1..5 ("checkers") compute the upstream-candidate mask of tasks
+// j = first + w + 5k: the segment-overlap test of Alg. 1 (extended to RAW) of
+// task j against its W - 1 predecessors, one predecessor per lane, ballot ->
+// mask (bit i mod W for each conflicting i in [j - W + 1, j - 1]). The
+// candidate set of a task is fixed by the stream, so the test runs ahead of
+// execution, in parallel with it. Warp 6 polls the
+// done words of executing slots. Warp 7 loads descriptors. Warp 0 owns the
+// window: it inserts checked tasks into the W-slot ring, dispatching each at
+// once (its workers wait for the predecessors its mask names: the pending ->
+// ready transition happens at the worker), retires tasks the poller saw
+// complete and releases slots in program order.
 
 struct SchedShared {
     uint32_t complete_upto;  // hist holds every seq below (loaded), from `lo`
@@ -90,17 +94,10 @@ struct SchedShared {
     uint32_t end;            // stream end known to the CTA (grows while the stream is open)
 };
 
-struct DispatchEntry {
-    unsigned long long up;   // upstream slots the workers must still wait for
-    uint32_t n;              // ncta
-    uint32_t seq;
-    uint32_t end;            // inclusive prefix of n over ranks
-    uint32_t pad;
-};
-
 struct SchedSmem {
-    DispatchEntry *disp;     // [32] tasks of the current dispatch batch, by age
-    TaskRec *hist;
+    unsigned long long *retired;  // slots the poller saw retire, not yet taken by warp 0
+    uint32_t *expect;        // [kMaxWindow] done value of each executing slot (0: none)
+    HistRec *hist;
     unsigned long long *pmask;
     uint32_t *ptag;
     SchedShared *sh;
@@ -111,15 +108,17 @@ __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     SchedSmem s;
     s.H = hist_size(W);
     uint8_t *p = smem;
-    s.hist = reinterpret_cast<TaskRec *>(p);
-    p += s.H * sizeof(TaskRec);
+    s.hist = reinterpret_cast<HistRec *>(p);
+    p += s.H * sizeof(HistRec);
     s.pmask = reinterpret_cast<unsigned long long *>(p);
     p += s.H * sizeof(unsigned long long);
     s.ptag = reinterpret_cast<uint32_t *>(p);
     p += s.H * sizeof(uint32_t);
     s.sh = reinterpret_cast<SchedShared *>(p);
     p += sizeof(SchedShared);
-    s.disp = reinterpret_cast<DispatchEntry *>(p);
+    s.retired = reinterpret_cast<unsigned long long *>(p);
+    p += sizeof(unsigned long long);
+    s.expect = reinterpret_cast<uint32_t *>(p);
     return s;
 }
 
@@ -128,16 +127,39 @@ __device__ __forceinline__ void sts_volatile(uint32_t *p, uint32_t v) { *(volati
 
 // Alg. 1's overlap test between task i (earlier) and task j on inclusive
 // ranges; a segment pair counts unless both are reads (RAW, WAR, WAW).
-__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const TaskRec &rj) {
-    const int ni = min((int)ri.nseg, kMaxSegs), nj = min((int)rj.nseg, kMaxSegs);
-    const uint32_t wi = ri.wmask, wj = rj.wmask;
+// The task being checked, its first kRegSegs segments held in registers
+// (the same for every lane; tasks with more segments read the rest from
+// shared memory).
+constexpr int kRegSegs = 6;
+struct NewTask {
+    Seg a[kRegSegs];
+    uint32_t n, w;
+};
+
+__device__ __forceinline__ NewTask load_new_task(const TaskRec &rj) {
+    NewTask t;
+    t.n = min((uint32_t)rj.nseg, (uint32_t)kMaxSegs);
+    t.w = rj.wmask;
+#pragma unroll
+    for (int x = 0; x < kRegSegs; ++x) t.a[x] = x < (int)t.n ? rj.seg[x] : Seg{0, 0};   // unused beyond n
+    return t;
+}
+
+__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const NewTask &t, const TaskRec &rj) {
+    const int ni = min((int)ri.nseg, kMaxSegs);
+    const uint32_t wi = ri.wmask;
+    bool hit = false;
     for (int y = 0; y < ni; ++y) {
         const Seg b = ri.seg[y];
         const bool yw = (wi >> y) & 1u;
-        for (int x = 0; x < nj; ++x) {
+#pragma unroll
+        for (int x = 0; x < kRegSegs; ++x)
+            hit |= x < (int)t.n && (yw || ((t.w >> x) & 1u)) && t.a[x].start <= b.last && b.start <= t.a[x].last;
+        for (uint32_t x = kRegSegs; x < t.n; ++x) {
             const Seg a = rj.seg[x];
-            if ((yw || ((wj >> x) & 1u)) && a.start <= b.last && b.start <= a.last) return true;
+            hit |= (yw || ((t.w >> x) & 1u)) && a.start <= b.last && b.start <= a.last;
         }
+        if (hit) return true;
     }
     return false;
 }
@@ -182,10 +204,13 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
             } else {
                 tw = 0;
                 backoff = 32;
-                const uint32_t n16 = (bhi - load_upto) * (uint32_t)(sizeof(TaskRec) / 16);
+                constexpr uint32_t kRec16 = sizeof(TaskRec) / 16;    // 20 vectors per record
+                const uint32_t n16 = (bhi - load_upto) * kRec16;
                 const uint4 *src = reinterpret_cast<const uint4 *>(recs + (load_upto & (C - 1)));
-                uint4 *dst = reinterpret_cast<uint4 *>(&S.hist[load_upto & HM]);
-                for (uint32_t i = lane; i < n16; i += 32) dst[i] = __ldcg(src + i);
+                for (uint32_t i = lane; i < n16; i += 32) {
+                    const uint32_t rec = i / kRec16, part = i - rec * kRec16;
+                    reinterpret_cast<uint4 *>(&S.hist[(load_upto + rec) & HM])[part] = __ldcg(src + i);
+                }
                 __syncwarp();
                 __threadfence_block();
                 load_upto = bhi;
@@ -208,6 +233,42 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     }
 }
 
+// Warp 6: polls the done word of every executing slot (relaxed loads) and
+// posts the slots whose task retired into a shared bitmask; the acquire fence
+// it executes before posting, with warp 0's fence before it publishes work,
+// orders the retired tasks' writes before every dependent's start. Warp 0
+// never waits on global memory to retire tasks.
+__device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t W = P.window;
+    SchedSmem S = carve(smem_raw, W);
+    const uint32_t *done = P.done + stream * kMaxWindow;
+    uint32_t backoff = 32;
+    while (!lds_volatile(&S.sh->quit)) {
+        const uint32_t e0 = lane < W ? lds_volatile(&S.expect[lane]) : 0u;
+        const uint32_t e1 = lane + 32 < W ? lds_volatile(&S.expect[lane + 32]) : 0u;
+        bool h0 = false, h1 = false;
+        if (e0) h0 = (int32_t)(ld_relaxed_u32(&done[lane]) - e0) >= 0;
+        if (e1) h1 = (int32_t)(ld_relaxed_u32(&done[lane + 32]) - e1) >= 0;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+        if (b0 | b1) {
+            fence_acq_rel_gpu();                 // acquire: the retired tasks' writes
+            if (h0) sts_volatile(&S.expect[lane], 0u);
+            if (h1) sts_volatile(&S.expect[lane + 32], 0u);
+            __threadfence_block();
+            if (lane == 0) atomicOr(S.retired, (unsigned long long)b0 | ((unsigned long long)b1 << 32));
+            __syncwarp();
+            backoff = 32;
+        } else {
+            const bool any = __any_sync(0xffffffffu, e0 | e1);
+            if (!any) {
+                __nanosleep(backoff);
+                if (backoff < 256) backoff <<= 1;
+            }
+        }
+    }
+}
+
 __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw, uint32_t w) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
@@ -215,9 +276,10 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     const bool open = P.open[stream] != 0;         // then tasks beyond `end` may still come
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
-    constexpr uint32_t kCheckers = kBlock / 32 - 2;   // warps 1 .. 6
+    constexpr uint32_t kCheckers = kBlock / 32 - 3;   // warps 1 .. 5
     unsigned long long tw = 0;
-    unsigned long long seg_bytes = 0;
+    unsigned long long seg_bytes = 0, check_cycles = 0;
+    const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     for (uint32_t j = first + w; open || j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
         uint32_t spins = 0, backoff = 32;
@@ -227,6 +289,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             if (cu > j && j < nx + H) break;
             if (lds_volatile(&S.sh->quit)) {
                 if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
+                if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
                 return;
             }
             if ((++spins & 63) == 0) {
@@ -241,21 +304,23 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             if (backoff < 256) backoff <<= 1;
         }
         if (lane == 0) {   // algorithmic bytes: what the task's segments name
-            const TaskRec &rr = S.hist[j & HM];
+            const TaskRec &rr = S.hist[j & HM].r;
             for (uint32_t k = 0; k < rr.nseg && k < (uint32_t)kMaxSegs; ++k)
                 if (!(rr.seg[k].start == 0 && rr.seg[k].last == ~0ull)) seg_bytes += rr.seg[k].last - rr.seg[k].start + 1;
         }
         tw = 0;
         __threadfence_block();
-        const TaskRec &rj = S.hist[j & HM];
+        const unsigned long long tc0 = tracing ? clock64() : 0ull;
+        const TaskRec &rj = S.hist[j & HM].r;
         if (rj.seq != j || rj.nseg > kMaxSegs) {   // self-check: the record must be task j
             if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteCheckRecord);
             return;
         }
         bool c0 = false, c1 = false;
         const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
-        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM], rj);
-        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM], rj);
+        const NewTask nt = load_new_task(rj);
+        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM].r, nt, rj);
+        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM].r, nt, rj);
         const uint32_t b0 = __ballot_sync(0xffffffffu, c0);
         const uint32_t b1 = __ballot_sync(0xffffffffu, c1);
         if (lane == 0) {
@@ -273,10 +338,12 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             S.pmask[j & HM] = m;
             __threadfence_block();
             sts_volatile(&S.ptag[j & HM], j + 1u);
+            if (tracing) check_cycles += clock64() - tc0;
         }
         __syncwarp();
     }
     if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
+    if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
 }
 
 // Shared-memory set-up of a scheduler CTA, before its warps take their roles
@@ -286,7 +353,9 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     const uint32_t first = P.first[stream];
     SchedSmem S = carve(smem_raw, W);
     for (uint32_t i = threadIdx.x; i < S.H; i += blockDim.x) S.ptag[i] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kMaxWindow; i += blockDim.x) S.expect[i] = 0;
     if (threadIdx.x == 0) {
+        *S.retired = 0ull;
         S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
         S.sh->next = first;
         S.sh->quit = 0;
@@ -308,7 +377,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const uint32_t first = P.first[stream];
     const bool open = P.open[stream] != 0;
     uint32_t end = P.end[stream];              // grows while the stream is open
-    uint32_t *done = P.done + stream * kMaxWindow;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const uint32_t LM = (1u << P.log_log2) - 1u;
@@ -316,11 +384,10 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;
     const unsigned long long t_begin = clock64();
-    unsigned long long busy = 0, inserts = 0;
+    unsigned long long busy = 0, inserts = 0, starved = 0;
 
     // per-lane slot registers: slot lane (index 0) and lane + 32 (index 1)
-    uint32_t st0 = kEmpty, st1 = kEmpty, sq0 = 0, sq1 = 0, nc0 = 0, nc1 = 0;
-    unsigned long long mk0 = 0, mk1 = 0;
+    uint32_t st0 = kEmpty, st1 = kEmpty, sq0 = 0, sq1 = 0;
 
     uint32_t head = first, next = first;
     uint32_t hslot = first % W, nslot = first % W;   // head % W, next % W
@@ -336,12 +403,13 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     bool failed = false;
     unsigned long long ph[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long tp = 0;
-#define ACS_PHASE(k) do { const unsigned long long _t = clock64(); ph[k] += _t - tp; tp = _t; } while (0)
+// per-phase cycle counters, only when tracing (each clock read sits on the warp's path)
+#define ACS_PHASE(k) do { if (tracing) { const unsigned long long _t = clock64(); ph[k] += _t - tp; tp = _t; } } while (0)
 
     uint32_t head_pub = first;
     while (first < end || open) {
         bool progress = false;
-        const unsigned long long t0 = clock64();
+        const unsigned long long t0 = tracing ? clock64() : 0ull;
         tp = t0;
         if (open) end = lds_volatile(&S.sh->end);
 
@@ -356,165 +424,32 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             const uint32_t okm = __ballot_sync(0xffffffffu, ok);
             nins = __ffs(~okm) - 1;          // leading run of checked tasks
             if (okm == 0xffffffffu) nins = 32;
+            if (tracing && nins == 0 && cap > 0) ++starved;
         }
         if (nins) __threadfence_block();
 
-        // 2. issue the done-word loads of executing slots; their latency
-        //    overlaps the inserts
-        uint32_t dv0 = 0, dv1 = 0;
-        if (st0 == kExec) dv0 = ld_relaxed_u32(&done[lane]);
-        if (st1 == kExec) dv1 = ld_relaxed_u32(&done[lane + 32u]);
-
         const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
-        // 3. insert, lane k taking task next + k: upstream = its candidates
-        //    still active, the new tasks before it included
+        // values of this iteration's insertion batch, published after retire
+        bool mine = false;
+        uint32_t q = 0, my_n = 0, my_off = 0, js = 0, p0 = 0;
+        // 2. insert and dispatch, lane k taking task next + k. Every task is
+        //    dispatched when it enters the window: its worker CTAs wait for the
+        //    checker's mask and then for the done words of the predecessors it
+        //    names. Units enter the FIFO work ring in program order, after
+        //    those of every upstream task, so the oldest unfinished unit never
+        //    waits on a later one: no deadlock.
         if (nins) {
-            unsigned long long act = __ballot_sync(0xffffffffu, st0 == kPending || st0 == kReady || st0 == kExec);
-            if (W > 32)
-                act |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kPending || st1 == kReady || st1 == kExec) << 32;
-            const bool mine = lane < nins;
-            const uint32_t q = next + lane;
+            mine = lane < nins;
+            q = next + lane;
+            my_n = mine ? (uint32_t)S.hist[q & HM].r.ncta : 0u;
+            // upstream = candidates still active (older new tasks included);
+            // retired ones are covered by the release below
+            unsigned long long act = __ballot_sync(0xffffffffu, st0 == kExec);
+            if (W > 32) act |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kExec) << 32;
             const unsigned long long pre = mine ? S.pmask[q & HM] : 0ull;
-            const uint32_t ncta = mine ? S.hist[q & HM].ncta : 0u;
-            // slots nslot .. nslot + lane - 1 (mod W) hold the earlier new tasks
             const unsigned long long low = (1ull << lane) - 1ull;
             const unsigned long long newer = nslot ? (((low << nslot) | (low >> (W - nslot))) & full) : low;
             const unsigned long long up = pre & (act | newer);
-            if (mine && (logging || tracing)) {
-                const size_t li = lbase + (q & LM);
-                if (logging) {
-                    P.log_mask[li] = pre;
-                    P.log_start[li] = ~0ull;
-                    P.log_retire[li] = 0ull;
-                }
-                if (tracing) {
-                    P.trace[li * kTraceFields + 0] = globaltimer_ns();
-                    P.trace[li * kTraceFields + 2] = ~0ull;   // first-CTA start: atomicMin target
-                }
-            }
-            // hand each task to the lane owning its slot
-            const uint32_t k0 = lane >= nslot ? lane - nslot : lane + W - nslot;
-            const uint32_t u0l = __shfl_sync(0xffffffffu, (uint32_t)up, k0 & 31);
-            const uint32_t u0h = __shfl_sync(0xffffffffu, (uint32_t)(up >> 32), k0 & 31);
-            const uint32_t n0 = __shfl_sync(0xffffffffu, ncta, k0 & 31);
-            if (lane < W && k0 < nins) {
-                mk0 = (unsigned long long)u0l | ((unsigned long long)u0h << 32);
-                st0 = mk0 ? kPending : kReady;
-                sq0 = next + k0;
-                nc0 = n0;
-            }
-            if (W > 32) {
-                const uint32_t s1 = lane + 32u;
-                const uint32_t k1 = s1 >= nslot ? s1 - nslot : s1 + W - nslot;
-                const uint32_t u1l = __shfl_sync(0xffffffffu, (uint32_t)up, k1 & 31);
-                const uint32_t u1h = __shfl_sync(0xffffffffu, (uint32_t)(up >> 32), k1 & 31);
-                const uint32_t n1 = __shfl_sync(0xffffffffu, ncta, k1 & 31);
-                if (s1 < W && k1 < nins) {
-                    mk1 = (unsigned long long)u1l | ((unsigned long long)u1h << 32);
-                    st1 = mk1 ? kPending : kReady;
-                    sq1 = next + k1;
-                    nc1 = n1;
-                }
-            }
-            next += nins;
-            nslot += nins;
-            if (nslot >= W) nslot -= W;
-            inserts += nins;
-            progress = true;
-            if (lane == 0) sts_volatile(&S.sh->next, next);
-        }
-        ACS_PHASE(1);
-
-        // 4. retire: a slot retires when its done word reads seq + 1
-        const bool ret0 = st0 == kExec && dv0 == sq0 + 1u;
-        const bool ret1 = st1 == kExec && dv1 == sq1 + 1u;
-        unsigned long long R = __ballot_sync(0xffffffffu, ret0);
-        if (W > 32) R |= (unsigned long long)__ballot_sync(0xffffffffu, ret1) << 32;
-        if (R) {
-            progress = true;
-            mk0 &= ~R;
-            mk1 &= ~R;
-            if (ret0) st0 = kRetired;
-            if (ret1) st1 = kRetired;
-            if (st0 == kPending && mk0 == 0) st0 = kReady;
-            if (st1 == kPending && mk1 == 0) st1 = kReady;
-            if (tracing) {
-                const unsigned long long now = globaltimer_ns();
-                if (ret0) P.trace[(lbase + (sq0 & LM)) * kTraceFields + 4] = now;
-                if (ret1) P.trace[(lbase + (sq1 & LM)) * kTraceFields + 4] = now;
-            }
-            // release in program order: the run of retired slots from the head
-            unsigned long long RT = __ballot_sync(0xffffffffu, st0 == kRetired);
-            if (W > 32) RT |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kRetired) << 32;
-            const unsigned long long rrt = hslot ? (((RT >> hslot) | (RT << (W - hslot))) & full) : RT;
-            uint32_t run = rrt == ~0ull ? 64u : (uint32_t)(__ffsll((long long)~rrt) - 1);
-            run = min(run, next - head);
-            head += run;
-            hslot += run;
-            if (hslot >= W) hslot -= W;
-        }
-        ACS_PHASE(2);
-        if (open && head != head_pub && lane == 0) {   // emitters wait on it for ring space
-            st_relaxed_u32(&P.sctl[stream].head_pub, head);
-        }
-        head_pub = head;
-        if (head == end) {
-            if (!open) { busy += clock64() - t0; break; }
-            // open stream: finished once no emitter is left and nothing was appended
-            uint32_t fin = 0;
-            if (lane == 0 && ld_relaxed_u32(&P.sctl[stream].open) == 0) {
-                fence_acq_rel_gpu();
-                fin = ld_relaxed_u32(&P.sctl[stream].end) == end;
-            }
-            if (__shfl_sync(0xffffffffu, fin, 0)) { busy += clock64() - t0; break; }
-        }
-
-        // 5. dispatch, oldest first, at most 32 undispatched tasks whose active
-        //    upstream tasks are all dispatched (or in this batch). A task still
-        //    pending carries its upstream mask in the cell; its worker CTAs
-        //    wait on those done words themselves, so no retire -> dispatch
-        //    relay through this warp sits on a dependency chain. Units enter
-        //    the FIFO ring after their upstream tasks' units, which keeps the
-        //    waits deadlock-free: the oldest unfinished unit never waits.
-        const bool nd0 = st0 == kPending || st0 == kReady;
-        const bool nd1 = st1 == kPending || st1 == kReady;
-        unsigned long long undisp = __ballot_sync(0xffffffffu, nd0);
-        if (W > 32) undisp |= (unsigned long long)__ballot_sync(0xffffffffu, nd1) << 32;
-        unsigned long long sel = 0;
-        while (undisp & ~sel) {
-            const unsigned long long waiting = undisp & ~sel;
-            const bool e0 = nd0 && !((sel >> lane) & 1ull) && (mk0 & waiting) == 0;
-            const bool e1 = nd1 && !((sel >> (lane + 32)) & 1ull) && (mk1 & waiting) == 0;
-            unsigned long long nw = __ballot_sync(0xffffffffu, e0);
-            if (W > 32) nw |= (unsigned long long)__ballot_sync(0xffffffffu, e1) << 32;
-            if (!nw) break;
-            sel |= nw;
-        }
-        if (sel) {
-            progress = true;
-            const uint32_t hs = hslot;
-            unsigned long long rot = hs ? (((sel >> hs) | (sel << (W - hs))) & full) : sel;   // bit a: age a
-            while (__popcll(rot) > 32) rot &= ~(1ull << (63 - __clzll((long long)rot)));   // oldest 32
-            // owner lanes post (ncta, seq, upstream) under their age rank
-            DispatchEntry *D = S.disp;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t sl = lane + 32u * h;
-                if (sl < W) {
-                    const uint32_t age = sl >= hs ? sl - hs : sl + W - hs;
-                    if ((rot >> age) & 1ull) {
-                        const uint32_t rank = __popcll(rot & ((1ull << age) - 1ull));
-                        D[rank].n = h ? nc1 : nc0;
-                        D[rank].seq = h ? sq1 : sq0;
-                        D[rank].up = h ? mk1 : mk0;
-                        if (h) st1 = kExec; else st0 = kExec;
-                    }
-                }
-            }
-            __syncwarp();
-            const uint32_t nsel = __popcll(rot);
-            // ring offsets: inclusive prefix of ncta over ranks
-            const uint32_t my_n = lane < nsel ? D[lane].n : 0u;
             uint32_t incl = my_n;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -522,9 +457,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                 if (lane >= (uint32_t)o) incl += v;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane < nsel) D[lane].end = incl;
-            __syncwarp();
-            uint32_t p0;
             if (sole_producer) {
                 p0 = tail;
             } else {
@@ -557,49 +489,113 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
             if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
             ACS_PHASE(4);
-            // aux words (upstream mask still to wait for, seq), one fence, then
-            // the sequence words that publish the units: a worker acquiring its
-            // cell sees its aux word, and everything this warp acquired (done
-            // words of retired predecessors) happens before.
-            uint32_t urank[2] = {0, 0};
-            for (uint32_t u = lane, it2 = 0; u < total; u += 32, ++it2) {
-                uint32_t lo = 0, hi = nsel - 1;          // first rank with end > u
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (D[mid].end > u) hi = mid; else lo = mid + 1;
+            // aux words (upstream still to wait for, seq) and log entries, then
+            // one release fence, then the sequence words that publish the units.
+            // The fence also orders the retirements seen through the poller
+            // (which acquired those done words) before the new tasks: conflicts
+            // farther back than W - 1 rely on that alone.
+            js = nslot + lane >= W ? nslot + lane - W : nslot + lane;
+            my_off = incl - my_n;
+            if (mine) {
+                for (uint32_t c = 0; c < my_n; ++c) {
+                    CellAux *ax = &P.cellaux[(p0 + my_off + c) & P.cell_mask];
+                    ax->up = up;
+                    ax->seq = q;
                 }
-                if (it2 < 2) urank[it2] = lo;
-                CellAux *ax = &P.cellaux[(p0 + u) & P.cell_mask];
-                ax->up = D[lo].up;
-                ax->seq = D[lo].seq;
+                if (logging || tracing) {
+                    const size_t li = lbase + (q & LM);
+                    if (logging) {
+                        P.log_mask[li] = pre;
+                        P.log_start[li] = ~0ull;
+                        P.log_retire[li] = 0ull;
+                    }
+                    if (tracing) {
+                        const unsigned long long now = globaltimer_ns();
+                        P.trace[li * kTraceFields + 0] = now;
+                        P.trace[li * kTraceFields + 1] = now;
+                        P.trace[li * kTraceFields + 2] = ~0ull;   // first-CTA start: atomicMin target
+                    }
+                }
             }
             ACS_PHASE(5);
-            fence_acq_rel_gpu();   // also turns the relaxed done polls above into acquires
-            __syncwarp();          // ... for every lane's stores below, whichever lane polled
-            ACS_PHASE(6);
-            const unsigned long long tnow = tracing ? globaltimer_ns() : 0ull;
-            for (uint32_t u = lane, it2 = 0; u < total; u += 32, ++it2) {
-                uint32_t r;
-                if (it2 < 2) {
-                    r = urank[it2];
-                } else {
-                    uint32_t lo = 0, hi = nsel - 1;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (D[mid].end > u) hi = mid; else lo = mid + 1;
-                    }
-                    r = lo;
-                }
-                const uint32_t q = D[r].seq;
-                const uint32_t cta = u - (D[r].end - D[r].n);
-                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
-                const unsigned long long payload = ((unsigned long long)gidx << 8) | cta;
-                const uint32_t pos = p0 + u;
-                st_relaxed_u64(&P.cells[pos & P.cell_mask], (payload << 32) | (unsigned long long)(pos + 1u));
+            // slot states for in-order release: the owner of slot s takes task
+            // next + ((s - nslot) mod W)
+            const uint32_t k0 = lane >= nslot ? lane - nslot : lane + W - nslot;
+            if (lane < W && k0 < nins) { st0 = kExec; sq0 = next + k0; }
+            if (W > 32) {
+                const uint32_t s1 = lane + 32u;
+                const uint32_t k1 = s1 >= nslot ? s1 - nslot : s1 + W - nslot;
+                if (s1 < W && k1 < nins) { st1 = kExec; sq1 = next + k1; }
             }
-            if (tracing && lane < nsel) P.trace[(lbase + (D[lane].seq & LM)) * kTraceFields + 1] = tnow;
+            next += nins;
+            nslot += nins;
+            if (nslot >= W) nslot -= W;
+            inserts += nins;
+            progress = true;
+            if (lane == 0) sts_volatile(&S.sh->next, next);
             __syncwarp();
         }
+        ACS_PHASE(1);
+
+        // 4. retire the slots the poller warp saw complete
+        unsigned long long R = 0;
+        if (lane == 0) R = atomicExch(S.retired, 0ull);
+        R = ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(R >> 32), 0) << 32) |
+            __shfl_sync(0xffffffffu, (uint32_t)R, 0);
+        const bool ret0 = (R >> lane) & 1ull;
+        const bool ret1 = W > 32 && ((R >> (lane + 32)) & 1ull);
+        if (R) {
+            progress = true;
+            if (ret0) st0 = kRetired;
+            if (ret1) st1 = kRetired;
+            if (tracing) {
+                const unsigned long long now = globaltimer_ns();
+                if (ret0) P.trace[(lbase + (sq0 & LM)) * kTraceFields + 4] = now;
+                if (ret1) P.trace[(lbase + (sq1 & LM)) * kTraceFields + 4] = now;
+            }
+            // release in program order: the run of retired slots from the head
+            unsigned long long RT = __ballot_sync(0xffffffffu, st0 == kRetired);
+            if (W > 32) RT |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kRetired) << 32;
+            const unsigned long long rrt = hslot ? (((RT >> hslot) | (RT << (W - hslot))) & full) : RT;
+            uint32_t run = rrt == ~0ull ? 64u : (uint32_t)(__ffsll((long long)~rrt) - 1);
+            run = min(run, next - head);
+            head += run;
+            hslot += run;
+            if (hslot >= W) hslot -= W;
+        }
+        ACS_PHASE(2);
+        // 5. publish this iteration's insertion batch (the aux stores above had
+        //    the retire step to complete before the fence)
+        if (nins) {
+            fence_acq_rel_gpu();
+            __syncwarp();
+            ACS_PHASE(6);
+            if (mine) {
+                S.expect[js] = q + 1u;             // the poller watches the slot from now on
+                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
+                for (uint32_t c = 0; c < my_n; ++c) {
+                    const uint32_t pos = p0 + my_off + c;
+                    const uint32_t payload = (gidx << 8) | c;
+                    st_relaxed_u64(&P.cells[pos & P.cell_mask],
+                                   ((unsigned long long)payload << 32) | (unsigned long long)(pos + 1u));
+                }
+            }
+        }
+        if (open && head != head_pub && lane == 0) {   // emitters wait on it for ring space
+            st_relaxed_u32(&P.sctl[stream].head_pub, head);
+        }
+        head_pub = head;
+        if (head == end) {
+            if (!open) { if (tracing) busy += clock64() - t0; break; }
+            // open stream: finished once no emitter is left and nothing was appended
+            uint32_t fin = 0;
+            if (lane == 0 && ld_relaxed_u32(&P.sctl[stream].open) == 0) {
+                fence_acq_rel_gpu();
+                fin = ld_relaxed_u32(&P.sctl[stream].end) == end;
+            }
+            if (__shfl_sync(0xffffffffu, fin, 0)) { if (tracing) busy += clock64() - t0; break; }
+        }
+
         ACS_PHASE(7);
         // look at the next 64 cells for the following batch (sole producer)
         if (sole_producer) {
@@ -608,7 +604,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         }
 
         if (progress) {
-            busy += clock64() - t0;
+            if (tracing) busy += clock64() - t0;
             idle_since = 0;
         } else {
             const unsigned long long now = globaltimer_ns();
@@ -631,6 +627,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         ss->inserts += inserts;
         ss->iterations += iter;
         for (int k = 0; k < kPhases; ++k) ss->phase[k] += ph[k];
+        ss->starved_iters += starved;
         __threadfence();
         if (atomicAdd(&P.ctl->sched_done, 1u) == P.n_streams - 1u) {
             __threadfence();
@@ -809,6 +806,7 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
     const uint32_t lane = threadIdx.x & 31;
     while (true) {
         if (threadIdx.x == 0) {
+            // claim the next work-ring position and wait for its unit
             const uint32_t pos = atomicAdd(&P.ctl->ring_head, 1u);
             unsigned long long *cell = &P.cells[pos & P.cell_mask];
             uint32_t quit = 0, spins = 0, backoff = 32;
@@ -929,6 +927,7 @@ __global__ void __launch_bounds__(kBlock, 3) acs_persistent_kernel(const __grid_
         const uint32_t warp = threadIdx.x / 32;
         if (warp == 0) scheduler_warp(P, blockIdx.x, smem);
         else if (warp == kBlock / 32 - 1) loader_warp(P, blockIdx.x, smem);
+        else if (warp == kBlock / 32 - 2) poller_warp(P, blockIdx.x, smem);
         else checker_warp(P, blockIdx.x, smem, warp - 1);
     } else {
         worker_loop(P, smem);

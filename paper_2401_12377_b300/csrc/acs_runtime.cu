@@ -780,8 +780,11 @@ int acs_get_stats(acs_ctx *c, acs_stats *out) {
             c->stats.sched_iterations = 0;
             c->stats.device_seg_bytes = 0;
             for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] = 0;
+            c->stats.check_cycles = c->stats.starved_iters = 0;
             for (auto &x : ss) {
                 c->stats.device_seg_bytes += x.seg_bytes;
+                c->stats.check_cycles += x.check_cycles;
+                c->stats.starved_iters += x.starved_iters;
                 for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] += x.phase[k];
                 c->stats.sched_cycles += x.cycles;
                 c->stats.sched_busy_cycles += x.busy_cycles;

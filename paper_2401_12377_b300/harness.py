@@ -307,6 +307,8 @@ class RLEmitDriver:
     def run(self) -> int:
         """One complete run; returns the number of tasks the stream had."""
         before = self.ctx.stats()
+        # emitted tasks take task_id = their position, so ids continue from there
+        self.sim.next_id = before["tasks_flushed"] + before["tasks_emitted"]
         tasks = self.first_tasks()
         self.ctx.submit(tasks, self.bufs)
         self.ctx.flush()

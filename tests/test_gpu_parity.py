@@ -242,3 +242,17 @@ def test_rlsim_device_emission_matches_host_driven_outputs():
     out_host = bufs.download()
     for k in ("pos", "vel", "cont", "nisl"):
         assert np.array_equal(out_emit[k], out_host[k]), k
+
+
+def test_rlsim_device_emission_repeats_in_one_context():
+    p = sg.RLParams(n_env=32, steps=4)
+    sim = sg.RLSim(9, p)
+    host = sim.buffers(emit=True)
+    bufs = harness.DeviceBuffers(host)
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(9, sg.RLParams(n_env=32, steps=4)), emit=True)
+    with harness.Context(32, capacity=256) as ctx:        # small ring: wraps, emitters wait for space
+        drv = harness.RLEmitDriver(sim, bufs, ctx)
+        for _ in range(3):
+            bufs.upload(host)
+            assert drv.run() == len(o_tasks)
+            assert_same(bufs.download(), o_bufs, "repeated run")
