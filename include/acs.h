@@ -299,6 +299,11 @@ int acs_get_log(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n,
  */
 int acs_get_trace(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n, uint64_t *t);
 
+/* Position of `stream`: the number of tasks it has had so far (host submitted
+ * plus device appended, the latter known after acs_sync); the next task's seq.
+ * Errors: ACS_ERR_INVALID. */
+int acs_stream_tail(acs_ctx *ctx, uint32_t stream, uint32_t *tail);
+
 /* Copy the context's counters into *out (after acs_sync for device figures). */
 int acs_get_stats(acs_ctx *ctx, acs_stats *out);
 

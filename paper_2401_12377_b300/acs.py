@@ -76,7 +76,8 @@ ARGS_DTYPE = np.dtype([("op", "<u2"), ("ncta", "<u2"), ("reserved", "<u4"), ("by
 assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
-           "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_get_stats", "acs_graph_replay",
+           "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_stream_tail",
+           "acs_get_stats", "acs_graph_replay",
            "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc"]
 
 _lib = None
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
     lib.acs_get_log.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
                                 C.c_void_p]
     lib.acs_get_trace.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p]
+    lib.acs_stream_tail.argtypes = [C.c_void_p, C.c_uint32, P(C.c_uint32)]
     lib.acs_get_stats.argtypes = [C.c_void_p, P(acs_stats)]
     lib.acs_graph_replay.argtypes = [C.c_void_p]
     lib.acs_error.argtypes = [C.c_void_p]
@@ -203,6 +205,12 @@ def acs_get_trace(ctx, stream: int, first: int, n: int) -> np.ndarray:
     t = np.zeros((n, 5), np.uint64)
     check(load().acs_get_trace(ctx, stream, first, n, t.ctypes.data), "acs_get_trace")
     return t
+
+
+def acs_stream_tail(ctx, stream: int) -> int:
+    v = C.c_uint32()
+    check(load().acs_stream_tail(ctx, stream, C.byref(v)), "acs_stream_tail")
+    return v.value
 
 
 def acs_get_stats(ctx) -> acs_stats:

@@ -771,6 +771,12 @@ int acs_get_trace(acs_ctx *c, uint32_t stream, uint64_t first, uint32_t n, uint6
     return ACS_OK;
 }
 
+int acs_stream_tail(acs_ctx *c, uint32_t stream, uint32_t *tail) {
+    if (!c || !tail || stream >= c->S) return ACS_ERR_INVALID;
+    *tail = c->st[stream].submitted;
+    return ACS_OK;
+}
+
 int acs_get_stats(acs_ctx *c, acs_stats *out) {
     if (!c || !out) return ACS_ERR_INVALID;
     if (c->cfg.mode == ACS_MODE_WINDOW) {

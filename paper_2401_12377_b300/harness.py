@@ -182,6 +182,9 @@ class Context:
     def stats(self) -> dict:
         return acs.stats_dict(acs.acs_get_stats(self.h))
 
+    def tail(self, stream: int = 0) -> int:
+        return acs.acs_stream_tail(self.h, stream)
+
     def replay(self) -> None:
         acs.check(acs.acs_graph_replay(self.h), "acs_graph_replay")
 
@@ -280,8 +283,8 @@ class RLEmitDriver:
     later task is appended on the device by emit tasks, so the whole run is one
     flush, one persistent launch and one sync."""
 
-    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context):
-        self.sim, self.bufs, self.ctx = sim, bufs, ctx
+    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context, stream: int = 0):
+        self.sim, self.bufs, self.ctx, self.stream = sim, bufs, ctx, stream
         p = sim.p
         sc = sim.scalars()
         cfg = np.zeros(1, EMIT_CFG_DTYPE)
@@ -304,20 +307,75 @@ class RLEmitDriver:
             tasks.append(e)
         return tasks
 
+    def submit(self) -> int:
+        """Submit the run's first tasks to the context (no flush); returns the
+        stream position the run starts at."""
+        start = self.ctx.tail(self.stream)
+        # emitted tasks take task_id = their position, so ids continue from there
+        self.sim.next_id = start
+        self.ctx.submit(self.first_tasks(), self.bufs, stream=self.stream)
+        return start
+
     def run(self) -> int:
         """One complete run; returns the number of tasks the stream had."""
-        before = self.ctx.stats()
-        # emitted tasks take task_id = their position, so ids continue from there
-        self.sim.next_id = before["tasks_flushed"] + before["tasks_emitted"]
-        tasks = self.first_tasks()
-        self.ctx.submit(tasks, self.bufs)
+        start = self.submit()
         self.ctx.flush()
         self.ctx.sync()
-        after = self.ctx.stats()
-        return (after["tasks_flushed"] - before["tasks_flushed"]) + (after["tasks_emitted"] - before["tasks_emitted"])
+        return self.ctx.tail(self.stream) - start
 
 
 def _one_plan(kind: int, idx: int):
     import streamgen as sg
     return sg.RLPlan(np.array([kind], np.uint8), np.array([idx], np.uint32), np.array([1], np.uint16), 0,
                      np.array([0], np.uint32))
+
+
+# ---- many independent streams in one persistent launch ----------------------------------
+
+class BatchedWorkload:
+    """The streams of ``streamgen.batched_specs`` on one device: rigid-sphere
+    streams run with device-side emission, DNN streams are submitted whole;
+    every stream is one of the context's independent streams, so one flush
+    runs all of them in one persistent launch."""
+
+    def __init__(self, specs, ctx: Context):
+        import streamgen as sg
+        self.specs, self.ctx = specs, ctx
+        self.items = []
+        for i, sp in enumerate(specs):
+            if sp.kind == "rl":
+                sim = sg.RLSim(sp.seed, sp.rl)
+                host = sim.buffers(emit=True)
+                bufs = DeviceBuffers(host)
+                self.items.append(("rl", host, bufs, RLEmitDriver(sim, bufs, ctx, stream=i)))
+            else:
+                st = sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks,
+                                   weight_sets=min(sp.dnn_blocks, 24))
+                bufs = DeviceBuffers(st.buffers)
+                ids, packed = pack_tasks(st.tasks, bufs)
+                self.items.append(("dnn", st.buffers, bufs, (ids, packed)))
+
+    def reset(self) -> None:
+        for kind, host, bufs, _ in self.items:
+            bufs.upload(host)
+
+    def submit_all(self) -> None:
+        for i, (kind, host, bufs, drv) in enumerate(self.items):
+            if kind == "rl":
+                drv.submit()
+            else:
+                ids, packed = drv
+                start = self.ctx.tail(i)
+                # ids continue from the stream's position across repeated runs
+                self.ctx.submit_packed(ids + np.uint32(start), packed, stream=i)
+
+    def run(self) -> int:
+        """One pass over every stream (one flush); returns tasks run."""
+        before = [self.ctx.tail(i) for i in range(len(self.items))]
+        self.submit_all()
+        self.ctx.flush()
+        self.ctx.sync()
+        return sum(self.ctx.tail(i) - b for i, b in enumerate(before))
+
+    def outputs(self):
+        return [bufs.download() for _, _, bufs, _ in self.items]

@@ -134,7 +134,7 @@ def dnn_gate(seed: int, sample: int, block: int) -> int:
 
 
 def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
-               window: int = 32, task_id0: int = 0) -> Stream:
+               window: int = 32, task_id0: int = 0, weight_sets: int = 0) -> Stream:
     """Gated residual MLP inference for ``batch`` samples, in block-major order.
 
     Block k of sample s runs iff ``dnn_gate(seed, s, k)``; a run block is four
@@ -142,12 +142,14 @@ def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
     ``u_s = W2_k t_s`` (GEMV), ``h_s = h_s + (u_s + b2_k)``. Weights and biases
     ~ U[-1/16, 1/16), inputs ~ U[-1, 1). Activations are per sample, so the
     samples' chains are independent; weights are shared read-only. GEMV tasks
-    use 1..32 CTAs (seeded), the elementwise ones 1 CTA.
+    use 1..32 CTAs (seeded), the elementwise ones 1 CTA. With ``weight_sets``
+    > 0 block k uses weight set k mod weight_sets (long streams, bounded memory).
     """
     rng = np.random.default_rng(seed)
     H = hidden
-    W = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H, H)).astype(np.float32)
-    B = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H)).astype(np.float32)
+    nw = weight_sets if weight_sets > 0 else blocks
+    W = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H, H)).astype(np.float32)
+    B = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H)).astype(np.float32)
     h = rng.uniform(-1.0, 1.0, (batch, H)).astype(np.float32)
     bufs = {"W": W.reshape(-1), "B": B.reshape(-1), "h": h.reshape(-1),
             "t": np.zeros(batch * H, np.float32), "u": np.zeros(batch * H, np.float32)}
@@ -157,10 +159,11 @@ def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
         for s in range(batch):
             if not dnn_gate(seed, s, k):
                 continue
-            w1 = Ref("W", (k * 2 + 0) * H * H, H * H)
-            w2 = Ref("W", (k * 2 + 1) * H * H, H * H)
-            b1 = Ref("B", (k * 2 + 0) * H, H)
-            b2 = Ref("B", (k * 2 + 1) * H, H)
+            kw = k % nw
+            w1 = Ref("W", (kw * 2 + 0) * H * H, H * H)
+            w2 = Ref("W", (kw * 2 + 1) * H * H, H * H)
+            b1 = Ref("B", (kw * 2 + 0) * H, H)
+            b2 = Ref("B", (kw * 2 + 1) * H, H)
             hs, ts, us = Ref("h", s * H, H), Ref("t", s * H, H), Ref("u", s * H, H)
             c1 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 1) % len(GEMV_NCTA_CHOICES)]
             c2 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 2) % len(GEMV_NCTA_CHOICES)]
@@ -390,3 +393,36 @@ def sleep_chain_stream(n_tasks: int, sleep_ns: int, width: int, window: int = 32
 def loguniform_lengths(seed: int, n: int, lo: int = 100, hi: int = 5000) -> List[int]:
     rng = np.random.default_rng(seed)
     return [int(round(math.exp(x))) for x in rng.uniform(math.log(lo), math.log(hi), n)]
+
+
+@dataclass
+class BatchSpec:
+    """One stream of a batch: ``kind`` 'rl' (an emitting rigid-sphere run) or
+    'dnn' (gated residual MLP inference), sized to about ``target`` tasks by
+    whole simulation steps or whole blocks."""
+    kind: str
+    seed: int
+    target: int
+    rl: Optional[RLParams] = None
+    dnn_batch: int = 1
+    dnn_blocks: int = 24
+
+
+RL_BATCH_ENVS = 64          # environments of an RL stream in a batch (~75 tasks per step)
+
+
+def batched_specs(seed: int, n_streams: int = 64, lo: int = 100, hi: int = 5000) -> List[BatchSpec]:
+    """Independent streams of uneven length (log-uniform in [lo, hi] tasks),
+    alternating rigid-sphere and dynamic-DNN kinds."""
+    out = []
+    for i, L in enumerate(loguniform_lengths(seed, n_streams, lo, hi)):
+        sseed = mix(seed, 0xB7, i) & 0xFFFFFFFF
+        if i % 2 == 0:
+            per_step = RL_BATCH_ENVS + 2 * (RL_BATCH_ENVS // 8) + 1
+            steps = max(1, int(round(L / per_step)))
+            out.append(BatchSpec("rl", sseed, L, rl=RLParams(n_env=RL_BATCH_ENVS, steps=steps)))
+        else:
+            b = 1 + (i // 2) % 8
+            blocks = max(1, int(round(L / (2 * b))))      # ~4 tasks per sample for half the blocks
+            out.append(BatchSpec("dnn", sseed, L, dnn_batch=b, dnn_blocks=blocks))
+    return out

@@ -1,0 +1,95 @@
+"""Many independent streams of uneven length in one persistent launch (the
+batched configuration): per stream, the window DAG, legality and outputs
+against the oracle; repeated runs in one context; the autotuner's choice and
+cache. GPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import streamgen as sg
+from oracle import addresses, deps, execute
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2401_12377_b300 import build
+    build.build()
+    from paper_2401_12377_b300 import autotune, harness
+
+DNN_RTOL = 1e-5
+
+
+def _oracle(sp):
+    if sp.kind == "rl":
+        t, b, _ = execute.run_rlsim(sg.RLSim(sp.seed, sp.rl), emit=True)
+        return t, b
+    s = sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks, weight_sets=min(sp.dnn_blocks, 24))
+    return s.tasks, execute.run_inorder(s.buffers, s.tasks)
+
+
+@pytest.mark.parametrize("W", [8, 32])
+def test_batched_streams_parity(W):
+    specs = sg.batched_specs(3, n_streams=8, lo=40, hi=400)
+    with harness.Context(W, n_streams=len(specs), log=True, capacity=1 << 12) as ctx:
+        wl = harness.BatchedWorkload(specs, ctx)
+        n = wl.run()
+        outs = wl.outputs()
+        assert ctx.stats()["launches"] == 1
+        total = 0
+        for i, sp in enumerate(specs):
+            o_tasks, o_bufs = _oracle(sp)
+            m = ctx.tail(i)
+            assert m == len(o_tasks), (i, sp.kind)
+            total += m
+            masks, start, retire = ctx.log(i, 0, m)
+            segs = addresses.stream_segments(o_tasks, o_bufs)
+            E = deps.full_dag(segs)
+            assert deps.edges_from_masks([int(x) for x in masks], W) == deps.window_dag(E, W), i
+            assert not deps.check_legal(E, [int(x) for x in start], [int(x) for x in retire]), i
+            for k in o_bufs:
+                g, o = outs[i][k], o_bufs[k]
+                if sp.kind == "rl" or o.dtype != np.float32:
+                    assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
+                else:
+                    scale = max(float(np.abs(o).max()), 1e-30)
+                    assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+        assert n == total
+
+
+def test_batched_repeats_in_one_context():
+    specs = sg.batched_specs(5, n_streams=6, lo=40, hi=300)
+    with harness.Context(16, n_streams=len(specs), capacity=1 << 12) as ctx:
+        wl = harness.BatchedWorkload(specs, ctx)
+        n1 = wl.run()
+        first = wl.outputs()
+        wl.reset()
+        n2 = wl.run()
+        second = wl.outputs()
+    assert n1 == n2
+    for a, b in zip(first, second):
+        for k in a:
+            assert np.array_equal(a[k].view(np.uint8), b[k].view(np.uint8)), k
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    specs = sg.batched_specs(7, n_streams=4, lo=40, hi=200)
+
+    def make_run(ctx):
+        wl = harness.BatchedWorkload(specs, ctx)
+
+        def run():
+            wl.reset()
+            return wl.run()
+        return run
+
+    path = str(tmp_path / "tune.json")
+    res = autotune.tune("test-batched-4", make_run, n_streams=4, windows=(8, 32), slots=(16, 64),
+                        repeats=2, path=path)
+    assert {(r["window"], r["cta_slots"]) for r in res["table"]} == {(8, 16), (8, 64), (32, 16), (32, 64)}
+    assert res["ms"] == min(r["ms"] for r in res["table"])
+    again = autotune.tune("test-batched-4", make_run, n_streams=4, path=path)
+    assert again["cached"] and again["window"] == res["window"] and again["cta_slots"] == res["cta_slots"]
+    assert json.load(open(path))
