@@ -41,6 +41,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
+WORKLOAD_BATCHED = ("batched: 64 independent streams (alternating rigid-sphere 64 envs x 32 spheres / gated "
+                    "residual MLP hidden 256, batch 1-8), lengths log-uniform in [100, 5000] tasks, one launch")
 
 
 def parse():
@@ -49,8 +51,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["acs", "reference"], default="acs")
-    ap.add_argument("--window", type=int, default=32)
+    ap.add_argument("--workload", choices=["rlsim", "batched"], default="rlsim",
+                    help="rlsim: one rigid-sphere stream (default); batched: 64 independent streams in one launch")
+    ap.add_argument("--window", type=int, default=0, help="window size (default: 32, or autotuned for batched)")
     ap.add_argument("--cta-slots", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--no-baselines", action="store_true", help="skip the in-order / graph arms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     return ap.parse_args()
@@ -81,6 +86,29 @@ def cpu_oracle_rate(budget_s: float = 10.0, max_runs: int = 20):
                       f"single-threaded numpy + C bodies, {dt:.1f} s"}
 
 
+def oracle_batch(seed: int, limit_s: float = 1e9):
+    """The oracle over the streams of one batch (in order, stream by stream),
+    stopping after the stream that crosses limit_s; returns (tasks, streams, s)."""
+    import streamgen as sg
+    from oracle import execute
+    execute.build_c()
+    tasks = streams = 0
+    t0 = time.perf_counter()
+    for sp in sg.batched_specs(seed):
+        if sp.kind == "rl":
+            t, _, _ = execute.run_rlsim(sg.RLSim(sp.seed, sp.rl), emit=True)
+        else:
+            st = sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks,
+                               weight_sets=min(sp.dnn_blocks, 24))
+            execute.run_inorder(st.buffers, st.tasks)
+            t = st.tasks
+        tasks += len(t)
+        streams += 1
+        if time.perf_counter() - t0 > limit_s:
+            break
+    return tasks, streams, time.perf_counter() - t0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -88,6 +116,24 @@ def run_reference(args):
     import streamgen as sg
     from oracle import execute
     execute.build_c()
+    if args.workload == "batched":
+        oracle_batch(100)   # warm-up: imports, compiled bodies
+        times, tasks = [], 0
+        for k in range(args.steps):
+            tasks, _, dt = oracle_batch(1 + k)
+            times.append(dt)
+        ms = 1e3 * statistics.mean(times)
+        value = tasks / (ms / 1e3)
+        line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD_BATCHED, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"each step one full batch of 64 streams ({tasks} tasks), "
+                                           "single-threaded"},
+                "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     for w in range(args.warmup):
         execute.run_rlsim(sg.RLSim(100 + w, rl_params(steps=5)))
     times, tasks = [], 0
@@ -274,6 +320,147 @@ def time_e2e(arm, steps):
             "ms_per_step": ms, "flushes_per_step": n_flush}
 
 
+class BatchArm:
+    """time_arm adapter for a batch (BatchedWorkload or BatchedHostDriven)."""
+
+    def __init__(self, torch, wl, ctx):
+        self.torch, self.wl, self.ctx = torch, wl, ctx
+
+    def reset_device(self):
+        self.wl.reset()
+
+    def run_once(self, latencies=None):
+        t0 = time.perf_counter()
+        n = self.wl.run()
+        if latencies is not None:
+            latencies.append(time.perf_counter() - t0)
+        return n
+
+
+def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+    """64 independent streams of uneven length in one persistent launch, window
+    and CTA slots from the autotuner; lockstep host-driven baselines."""
+    import streamgen as sg
+    from paper_2401_12377_b300 import autotune, harness
+    seed = 1 + rank
+    specs = sg.batched_specs(seed)
+    S = len(specs)
+    cap = 1 << 13
+    wl = harness.BatchedWorkload(specs, None)
+    tuned = None
+    if args.window or args.cta_slots or args.no_tune:
+        W, slots = args.window or 32, args.cta_slots
+    else:
+        def make_run(ctx):
+            wl.bind(ctx)
+
+            def run():
+                wl.reset()
+                return wl.run()
+            return run
+        t0 = time.perf_counter()
+        tuned = autotune.tune(f"{WORKLOAD_BATCHED}|seed={seed}", make_run, n_streams=S, repeats=5,
+                              capacity=cap)
+        tuned["tune_s"] = time.perf_counter() - t0
+        W, slots = tuned["window"], tuned["cta_slots"]
+    ctx = harness.Context(W, n_streams=S, cta_slots=slots, timing=True, capacity=cap)
+    wl.bind(ctx)
+    arm = BatchArm(torch, wl, ctx)
+    latencies = []
+    if dist:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = time_arm(arm, args.steps, args.warmup, flush_buf, latencies)
+    clocks = clk.summary()
+    ms_step = statistics.mean(res["ms"])
+    tasks_per_step = res["tasks"] / args.steps
+    max_ms = ms_step
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    st = res["stats"]
+    launches = st["launches"]
+    avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
+    bytes_per_launch = st["device_seg_bytes"] / max(1, launches)
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    line = {"metric": METRIC, "value": world * tasks_per_step / (max_ms / 1e3), "unit": "tasks/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_BATCHED, "streams": S, "window": W, "tasks_per_step": tasks_per_step,
+                       "cta_slots": st.get("cta_slots"), "grid": st.get("grid"),
+                       "stream_lengths": [sp.target for sp in specs],
+                       "mode": "window scheduler, one flush and one persistent launch for all streams",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"independent batches x{world}" if world > 1 else "one GPU"},
+            "autotune": None if tuned is None else {
+                "window": W, "cta_slots": slots, "tune_s": tuned.get("tune_s"), "cached": tuned.get("cached", False),
+                "table": [(r["window"], r["cta_slots"], round(r["ms"], 4)) for r in tuned.get("table", [])]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "acs_persistent_kernel",
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "avg_launch_us": avg_launch_s * 1e6,
+                         "note": "bytes named by the tasks' read+write segments per launch / mean launch time"},
+            "sched_cycles_per_task": st["sched_cycles"] / max(1, st["sched_inserts"]),
+            "gpu_launches": int(launches), "clocks": clocks}
+
+    if not args.no_baselines:
+        steps_b = max(1, min(args.steps, 3))
+        for mode, key in (("window", "window_host_driven"), ("inorder", "inorder"), ("graph", "graph")):
+            c2 = harness.Context(W, mode=mode, n_streams=S, cta_slots=slots, timing=True, capacity=cap)
+            hd = harness.BatchedHostDriven(specs, c2)
+            r = time_arm(BatchArm(torch, hd, c2), steps_b, 1, flush_buf)
+            ms = statistics.mean(r["ms"])
+            tps = r["tasks"] / steps_b
+            entry = {"tasks_per_s": tps / (ms / 1e3), "ms_per_step": ms, "flushes_per_step": hd.rounds,
+                     "kernel_ms_per_step": r["stats"]["kernel_ms"] / steps_b,
+                     "launches_per_step": r["stats"]["launches"] / steps_b}
+            if mode == "graph":
+                entry["host_build_instantiate_ms_per_step"] = (r["stats"]["graph_build_ms"]
+                                                               + r["stats"]["graph_instantiate_ms"]) / steps_b
+                line["graph_launch"] = {"tasks_per_s": tps / (entry["kernel_ms_per_step"] / 1e3),
+                                        "device_ms_per_step": entry["kernel_ms_per_step"],
+                                        "note": "graph launch device time only, build and round trips excluded"}
+                line["speedup_vs_graph_with_build"] = ms / ms_step
+                line["speedup_vs_graph_launch_only"] = entry["kernel_ms_per_step"] / ms_step
+                key = "graph_with_build"
+            elif mode == "inorder":
+                line["speedup_vs_inorder"] = ms / ms_step
+            line[key] = entry
+            c2.close()
+            del hd
+
+    # end to end: every stream's buffers in from pinned host memory, results out
+    reps = max(1, min(args.steps, 3))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wl.host_inputs()
+    wl.result_buffers()
+    torch.cuda.synchronize()
+    tasks = h2d = d2h = 0
+    ev0.record()
+    for _ in range(reps):
+        h2d += wl.upload_host()
+        tasks += wl.run()
+        d2h += wl.download_results()
+    ev1.record()
+    torch.cuda.synchronize()
+    e_ms = ev0.elapsed_time(ev1) / reps
+    desc = 320 * (tasks // reps)
+    line["e2e"] = {"value": (tasks / reps) / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": int(h2d // reps + desc), "d2h_bytes_per_step": int(d2h // reps)}
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        execute_tasks, n_streams, dt = oracle_batch(seed, limit_s=10.0)
+        line["cpu_baseline"] = {"value": execute_tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {n_streams} streams of the batch ({execute_tasks} tasks), "
+                                          f"single-threaded numpy + C bodies, {dt:.1f} s"}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -305,6 +492,15 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream())
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     seed = 1 + rank
+    if args.workload == "batched":
+        line = bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    args.window = args.window or 32
 
     # ---- the method: window scheduler with device-side emission (one launch per run) ----
     acs_arm = RLBench("window", seed, args.window, args.cta_slots, emit=True)

@@ -61,7 +61,7 @@ def max_worker_slots(window: int, n_streams: int) -> int:
 
 def tune(workload: str, make_run: Callable[[harness.Context], Callable[[], int]], n_streams: int,
          windows: Iterable[int] = DEFAULT_WINDOWS, slots: Iterable[int] = DEFAULT_SLOTS, repeats: int = 5,
-         warmup: int = 1, use_cache: bool = True, path: Optional[str] = None) -> dict:
+         warmup: int = 1, use_cache: bool = True, path: Optional[str] = None, capacity: int = 1 << 13) -> dict:
     """Pick (window, cta_slots) minimising the median device time of a run.
 
     ``make_run(ctx)`` prepares the workload on a context and returns a
@@ -77,7 +77,7 @@ def tune(workload: str, make_run: Callable[[harness.Context], Callable[[], int]]
     for W in windows:
         cap = max_worker_slots(W, n_streams)
         for sl in sorted({min(s, cap) for s in slots}):
-            with harness.Context(W, n_streams=n_streams, cta_slots=sl, timing=True, capacity=1 << 14) as ctx:
+            with harness.Context(W, n_streams=n_streams, cta_slots=sl, timing=True, capacity=capacity) as ctx:
                 run = make_run(ctx)
                 for _ in range(warmup):
                     run()

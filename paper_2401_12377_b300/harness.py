@@ -229,8 +229,8 @@ class RLDriver:
     the batch, sync, read back nisl (4 bytes per env) and emit the next plan.
     Packing is vectorised from per-env / per-chunk templates."""
 
-    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context):
-        self.sim, self.bufs, self.ctx = sim, bufs, ctx
+    def __init__(self, sim, bufs: DeviceBuffers, ctx: Context, stream: int = 0):
+        self.sim, self.bufs, self.ctx, self.stream = sim, bufs, ctx, stream
         p = sim.p
         sc = sim.scalars()
         self.templates = {}
@@ -253,18 +253,33 @@ class RLDriver:
         rows["ncta"] = plan.ncta
         return plan.ids, rows
 
-    def read_nisl(self) -> np.ndarray:
+    def start_read_nisl(self) -> None:
         self.nisl_host.copy_(self.bufs.t["nisl"].view(torch.int32), non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+
+    def nisl(self) -> np.ndarray:
+        """The island counts of the last start_read_nisl (after a stream sync)."""
         return self.nisl_host.numpy().view(np.uint32)
+
+    def read_nisl(self) -> np.ndarray:
+        self.start_read_nisl()
+        torch.cuda.current_stream().synchronize()
+        return self.nisl()
+
+    def begin(self):
+        """The first plan, numbered from the stream's current position."""
+        self.sim.next_id = self.ctx.tail(self.stream)
+        return self.sim.first_plan()
+
+    def submit_plan(self, plan) -> None:
+        self.ctx.submit_packed(*self.pack(plan), stream=self.stream)
 
     def run(self, record_plans: bool = False) -> List:
         plans = []
-        plan = self.sim.first_plan()
+        plan = self.begin()
         for t in range(self.sim.p.steps + 1):
             if t > 0:
                 plan = self.sim.step_plan(t - 1, self.read_nisl())
-            self.ctx.submit_packed(*self.pack(plan))
+            self.submit_plan(plan)
             self.ctx.flush()
             self.ctx.sync()
             if record_plans:
@@ -332,32 +347,99 @@ def _one_plan(kind: int, idx: int):
 
 # ---- many independent streams in one persistent launch ----------------------------------
 
-class BatchedWorkload:
+# buffers each kind of stream writes (the rest are read-only inputs)
+WRITTEN = {"rl": ("pos", "vel", "cont", "nisl", "token"), "dnn": ("h", "t", "u")}
+# what a caller reads back as the result of a stream
+RESULTS = {"rl": ("pos", "vel"), "dnn": ("h",)}
+
+
+class _Batch:
+    """Device buffers of every stream of a batch, with device-side pristine
+    copies of the written buffers (fast resets between runs) and pinned host
+    copies of every buffer (host-to-device runs)."""
+
+    def _add(self, kind, host, bufs, drv) -> None:
+        keep = {k: bufs.t[k].clone() for k in WRITTEN[kind] if k in bufs.t}
+        self.items.append((kind, host, bufs, drv))
+        self._pristine.append(keep)
+
+    def reset(self) -> None:
+        """Restore every written buffer to the stream's initial state (device copies)."""
+        for (_, _, bufs, _), keep in zip(self.items, self._pristine):
+            for k, v in keep.items():
+                bufs.t[k].copy_(v, non_blocking=True)
+
+    def host_inputs(self):
+        if self._pinned is None:
+            self._pinned = [{k: torch.from_numpy(np.ascontiguousarray(v).view(np.uint8).copy()).pin_memory()
+                             for k, v in host.items()} for _, host, _, _ in self.items]
+        return self._pinned
+
+    def upload_host(self) -> int:
+        """Copy every buffer of every stream from pinned host memory; returns bytes."""
+        n = 0
+        for (_, _, bufs, _), pin in zip(self.items, self.host_inputs()):
+            for k, v in pin.items():
+                bufs.t[k].copy_(v, non_blocking=True)
+                n += v.numel()
+        return n
+
+    def result_buffers(self):
+        """Pinned host tensors for each stream's result buffers."""
+        if self._results is None:
+            self._results = [{k: torch.empty(bufs.t[k].numel(), dtype=torch.uint8, pin_memory=True)
+                              for k in RESULTS[kind]} for kind, _, bufs, _ in self.items]
+        return self._results
+
+    def download_results(self) -> int:
+        """Start device-to-host copies of each stream's results; returns bytes."""
+        n = 0
+        for (_, _, bufs, _), out in zip(self.items, self.result_buffers()):
+            for k, v in out.items():
+                v.copy_(bufs.t[k], non_blocking=True)
+                n += v.numel()
+        return n
+
+    def outputs(self):
+        return [bufs.download() for _, _, bufs, _ in self.items]
+
+    def _init_common(self, specs, ctx) -> None:
+        self.specs, self.ctx = specs, ctx
+        self.items, self._pristine = [], []
+        self._pinned = self._results = None
+
+    @staticmethod
+    def _dnn(sp):
+        import streamgen as sg
+        return sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks, weight_sets=min(sp.dnn_blocks, 24))
+
+
+class BatchedWorkload(_Batch):
     """The streams of ``streamgen.batched_specs`` on one device: rigid-sphere
     streams run with device-side emission, DNN streams are submitted whole;
     every stream is one of the context's independent streams, so one flush
     runs all of them in one persistent launch."""
 
-    def __init__(self, specs, ctx: Context):
+    def __init__(self, specs, ctx: Optional[Context]):
         import streamgen as sg
-        self.specs, self.ctx = specs, ctx
-        self.items = []
+        self._init_common(specs, ctx)
         for i, sp in enumerate(specs):
             if sp.kind == "rl":
                 sim = sg.RLSim(sp.seed, sp.rl)
                 host = sim.buffers(emit=True)
                 bufs = DeviceBuffers(host)
-                self.items.append(("rl", host, bufs, RLEmitDriver(sim, bufs, ctx, stream=i)))
+                self._add("rl", host, bufs, RLEmitDriver(sim, bufs, ctx, stream=i))
             else:
-                st = sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks,
-                                   weight_sets=min(sp.dnn_blocks, 24))
+                st = self._dnn(sp)
                 bufs = DeviceBuffers(st.buffers)
-                ids, packed = pack_tasks(st.tasks, bufs)
-                self.items.append(("dnn", st.buffers, bufs, (ids, packed)))
+                self._add("dnn", st.buffers, bufs, pack_tasks(st.tasks, bufs))
 
-    def reset(self) -> None:
-        for kind, host, bufs, _ in self.items:
-            bufs.upload(host)
+    def bind(self, ctx: Context) -> None:
+        """Run the same streams (same device buffers) through another context."""
+        self.ctx = ctx
+        for kind, _, _, drv in self.items:
+            if kind == "rl":
+                drv.ctx = ctx
 
     def submit_all(self) -> None:
         for i, (kind, host, bufs, drv) in enumerate(self.items):
@@ -365,9 +447,8 @@ class BatchedWorkload:
                 drv.submit()
             else:
                 ids, packed = drv
-                start = self.ctx.tail(i)
                 # ids continue from the stream's position across repeated runs
-                self.ctx.submit_packed(ids + np.uint32(start), packed, stream=i)
+                self.ctx.submit_packed(ids + np.uint32(self.ctx.tail(i)), packed, stream=i)
 
     def run(self) -> int:
         """One pass over every stream (one flush); returns tasks run."""
@@ -377,5 +458,50 @@ class BatchedWorkload:
         self.ctx.sync()
         return sum(self.ctx.tail(i) - b for i, b in enumerate(before))
 
-    def outputs(self):
-        return [bufs.download() for _, _, bufs, _ in self.items]
+
+class BatchedHostDriven(_Batch):
+    """The streams of ``streamgen.batched_specs`` without device-side
+    emission, for the in-order and CUDA-graph baselines (which cannot emit) and
+    the host-driven window arm. Streams advance in lockstep rounds: round 0
+    submits every DNN stream whole and the first step of every rigid-sphere
+    stream; round t > 0 reads back the island counts of every rigid-sphere
+    stream that has a step t and submits that step. One flush and one sync per
+    round, over all streams."""
+
+    def __init__(self, specs, ctx: Context):
+        import streamgen as sg
+        self._init_common(specs, ctx)
+        for i, sp in enumerate(specs):
+            if sp.kind == "rl":
+                sim = sg.RLSim(sp.seed, sp.rl)
+                host = sim.buffers(emit=False)
+                bufs = DeviceBuffers(host)
+                self._add("rl", host, bufs, RLDriver(sim, bufs, ctx, stream=i))
+            else:
+                st = self._dnn(sp)
+                bufs = DeviceBuffers(st.buffers)
+                self._add("dnn", st.buffers, bufs, pack_tasks(st.tasks, bufs))
+        self.rounds = 1 + max([d.sim.p.steps for k, _, _, d in self.items if k == "rl"] or [0])
+
+    def run(self) -> int:
+        """One pass over every stream; returns tasks run."""
+        before = [self.ctx.tail(i) for i in range(len(self.items))]
+        rl = [(i, d) for i, (k, _, _, d) in enumerate(self.items) if k == "rl"]
+        for i, (kind, _, _, drv) in enumerate(self.items):
+            if kind == "dnn":
+                ids, packed = drv
+                self.ctx.submit_packed(ids + np.uint32(self.ctx.tail(i)), packed, stream=i)
+        for _, d in rl:
+            d.submit_plan(d.begin())
+        self.ctx.flush()
+        self.ctx.sync()
+        for t in range(1, self.rounds):
+            live = [d for _, d in rl if d.sim.p.steps >= t]
+            for d in live:
+                d.start_read_nisl()
+            torch.cuda.current_stream().synchronize()
+            for d in live:
+                d.submit_plan(d.sim.step_plan(t - 1, d.nisl()))
+            self.ctx.flush()
+            self.ctx.sync()
+        return sum(self.ctx.tail(i) - b for i, b in enumerate(before))

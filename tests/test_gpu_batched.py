@@ -59,6 +59,29 @@ def test_batched_streams_parity(W):
         assert n == total
 
 
+@pytest.mark.parametrize("mode", ["window", "inorder", "graph"])
+def test_batched_host_driven_outputs(mode):
+    """The lockstep host-driven form (the in-order and graph baselines) computes
+    the same results as the oracle."""
+    specs = sg.batched_specs(11, n_streams=6, lo=40, hi=300)
+    with harness.Context(16, mode=mode, n_streams=len(specs), capacity=1 << 12) as ctx:
+        wl = harness.BatchedHostDriven(specs, ctx)
+        n = wl.run()
+        outs = wl.outputs()
+    total = 0
+    for i, sp in enumerate(specs):
+        o_tasks, o_bufs = _oracle(sp)
+        total += len(o_tasks) - (sp.rl.steps if sp.kind == "rl" else 0)   # no emit tasks here
+        for k in outs[i]:
+            g, o = outs[i][k], o_bufs[k]
+            if sp.kind == "rl":
+                assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
+            else:
+                scale = max(float(np.abs(o).max()), 1e-30)
+                assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+    assert n == total
+
+
 def test_batched_repeats_in_one_context():
     specs = sg.batched_specs(5, n_streams=6, lo=40, hi=300)
     with harness.Context(16, n_streams=len(specs), capacity=1 << 12) as ctx:
