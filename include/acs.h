@@ -173,7 +173,10 @@ typedef struct acs_config {
     uint32_t ctas_per_sm;   /* cap on co-resident persistent CTAs per SM, enforced
                                through their shared-memory reservation (0 -> as
                                many as registers allow; a tuning knob) */
-    uint32_t reserved[5];   /* must be 0 */
+    uint32_t idle_limit_ms; /* resident launches (acs_start): the kernel leaves by
+                               itself after this long idle without any host call
+                               (0 -> 10 000 ms), so it always terminates */
+    uint32_t reserved[4];   /* must be 0 */
 } acs_config;
 
 typedef struct acs_stats {
@@ -303,6 +306,42 @@ int acs_get_trace(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n, uin
  * plus device appended, the latter known after acs_sync); the next task's seq.
  * Errors: ACS_ERR_INVALID. */
 int acs_stream_tail(acs_ctx *ctx, uint32_t stream, uint32_t *tail);
+
+/*
+ * Resident (serving) launches. acs_start launches the persistent scheduler
+ * kernel and leaves it on the device: every stream's window stays in its
+ * scheduler CTA between flushes, and new work reaches a running kernel with
+ * no launch. While resident:
+ *   - acs_submit / acs_submit_stream / acs_submit_ops stage descriptors in the
+ *     context's pinned host ring as before (ACS_ERR_FULL when the ring lacks
+ *     room for the task plus the window behind it: call acs_progress or
+ *     acs_sync, then retry);
+ *   - acs_flush publishes each stream's new end with one release store into
+ *     mapped host memory; no CUDA call. The kernel's loader warp copies the
+ *     descriptors over the bus into the device ring and schedules them;
+ *   - acs_progress reports, without blocking, per stream: head (tasks below
+ *     it were released, refreshed every 16 tasks and when idle) and idle_at
+ *     (the stream was last seen idle with this end: all tasks below it
+ *     retired and no emitter chain alive). Work published up to end E of a
+ *     stream is complete once idle_at >= E (mod 2^32); for a stream whose
+ *     flushed tasks hold emit tasks the tail (acs_stream_tail) then becomes
+ *     idle_at. The task outputs are visible to the host and to other CUDA
+ *     streams once idle_at covers them. A stream with emitter chains in
+ *     flight accepts no new tasks (ACS_ERR_INVALID) until that point;
+ *   - acs_sync waits on the host until every published task retired (bounded
+ *     by timeout_ns without progress) and leaves the kernel running.
+ * acs_start needs window mode, no launch in flight (acs_sync first), and
+ * publishes tasks already staged. acs_stop publishes what is staged, waits
+ * until all of it retired, and lets the kernel end (when nothing moves for
+ * timeout_ns it raises the device stop flag instead and returns
+ * ACS_ERR_TIMEOUT); acs_destroy stops a resident context first. The kernel
+ * also ends by itself after idle_limit_ms without any host call (then calls
+ * return ACS_ERR_STOPPED). Errors: ACS_ERR_INVALID, ACS_ERR_DEVICE, the
+ * device's first error.
+ */
+int acs_start(acs_ctx *ctx);
+int acs_progress(acs_ctx *ctx, uint32_t *head, uint32_t *idle_at);   /* arrays of n_streams, either NULL */
+int acs_stop(acs_ctx *ctx);
 
 /* Copy the context's counters into *out (after acs_sync for device figures). */
 int acs_get_stats(acs_ctx *ctx, acs_stats *out);

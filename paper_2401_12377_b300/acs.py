@@ -56,7 +56,8 @@ class acs_config(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("n_streams", C.c_uint32), ("cta_slots", C.c_uint32),
                 ("capacity", C.c_uint32), ("log_capacity", C.c_uint32), ("flags", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-                ("poll_ns", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+                ("poll_ns", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("idle_limit_ms", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class acs_stats(C.Structure):
@@ -77,7 +78,7 @@ assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
            "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_stream_tail",
-           "acs_get_stats", "acs_graph_replay",
+           "acs_get_stats", "acs_graph_replay", "acs_start", "acs_progress", "acs_stop",
            "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc"]
 
 _lib = None
@@ -109,6 +110,9 @@ def load(path: str = LIB_PATH):
     lib.acs_stream_tail.argtypes = [C.c_void_p, C.c_uint32, P(C.c_uint32)]
     lib.acs_get_stats.argtypes = [C.c_void_p, P(acs_stats)]
     lib.acs_graph_replay.argtypes = [C.c_void_p]
+    lib.acs_start.argtypes = [C.c_void_p]
+    lib.acs_progress.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.acs_stop.argtypes = [C.c_void_p]
     lib.acs_error.argtypes = [C.c_void_p]
     lib.acs_strerror.argtypes = [C.c_int]
     lib.acs_strerror.restype = C.c_char_p
@@ -211,6 +215,24 @@ def acs_stream_tail(ctx, stream: int) -> int:
     v = C.c_uint32()
     check(load().acs_stream_tail(ctx, stream, C.byref(v)), "acs_stream_tail")
     return v.value
+
+
+def acs_start(ctx) -> None:
+    check(load().acs_start(ctx), "acs_start")
+
+
+def acs_stop(ctx) -> None:
+    check(load().acs_stop(ctx), "acs_stop")
+
+
+def acs_progress(ctx, n_streams: int, head: np.ndarray = None, idle_at: np.ndarray = None):
+    """(head, idle_at) uint32 arrays of n_streams (filled in place when given)."""
+    if head is None:
+        head = np.zeros(n_streams, np.uint32)
+    if idle_at is None:
+        idle_at = np.zeros(n_streams, np.uint32)
+    check(load().acs_progress(ctx, head.ctypes.data, idle_at.ctypes.data), "acs_progress")
+    return head, idle_at
 
 
 def acs_get_stats(ctx) -> acs_stats:

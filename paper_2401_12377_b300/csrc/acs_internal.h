@@ -113,6 +113,27 @@ struct StreamCtl {
     uint32_t pad;
 };
 
+// Host-mapped words of a resident launch (pinned host memory the device reads
+// and writes over the bus). The host appends a stream's descriptors to its
+// pinned ring and then publishes the new end with a release store; the device
+// copies them into the device ring and reports progress back.
+struct StreamProgress {
+    uint32_t head;      // device -> host: tasks below were released (published every few tasks)
+    uint32_t idle_at;   // device -> host: the stream was idle (all tasks below retired,
+                        // no emitter alive) with this end
+};
+
+struct Mailbox {
+    uint32_t host_end[ACS_MAX_STREAMS];   // host -> device: published end of each stream
+    uint32_t drain;                       // host -> device: finish published work, then exit
+    uint32_t err;                         // device -> host: first error (as DevCtl::err)
+    uint32_t expired;                     // device -> host: exited after the idle limit
+    uint32_t pad0;
+    unsigned long long heartbeat;         // host -> device: changes with every host call
+    unsigned long long pad1[6];
+    StreamProgress progress[ACS_MAX_STREAMS];
+};
+
 // Second word of a work-ring cell: the upstream slots the unit's worker must
 // still wait for (bit b: the task in window slot b) and the task's seq.
 struct alignas(16) CellAux {
@@ -143,6 +164,10 @@ struct KParams {
     uint32_t flags;
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses
     uint32_t poll_ns;         // longest sleep of an idle worker between ring polls
+    uint32_t resident;        // 1: serve host-published work until drained (Mailbox)
+    Mailbox *mbox;            // mapped host memory (resident launches)
+    const TaskRec *host_recs; // device view of the pinned host rings [n_streams][capacity]
+    unsigned long long idle_limit_ns;  // resident: exit after this long without host activity
     uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
     uint32_t end[ACS_MAX_STREAMS];    // one past the last seq submitted by the host
     uint8_t open[ACS_MAX_STREAMS];    // emit tasks among the stream's new tasks

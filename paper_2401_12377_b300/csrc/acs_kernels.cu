@@ -55,9 +55,32 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     return v;
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// system scope: words in mapped host memory (resident launches)
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_sys_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint4 ld_volatile_v4(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_sys_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 __device__ __forceinline__ void raise_error(const KParams &P, uint32_t code, uint32_t site) {
-    if (atomicCAS(&P.ctl->err, 0u, code) == 0u) P.ctl->err_info = site;
+    if (atomicCAS(&P.ctl->err, 0u, code) == 0u) {
+        P.ctl->err_info = site;
+        if (P.resident) st_relaxed_sys_u32(&P.mbox->err, code);   // a waiting host sees it at once
+    }
     __threadfence();
     atomicExch(&P.ctl->stop, 1u);
 }
@@ -182,10 +205,49 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     uint32_t load_upto = first > W - 1 ? first - (W - 1) : 0u;
     unsigned long long tw = 0;
     uint32_t spins = 0, backoff = 32;
+    uint32_t host_seen = end;                      // resident: host end last read
     while (true) {
-        bool wait = false;
+        bool wait = false, host_wait = false;
         if (load_upto >= end) {
-            if (!open) return;                     // a closed stream is fully loaded
+            if (!open && !P.resident) return;      // a closed stream is fully loaded
+            if (P.resident) {
+                // host-published descriptors first: at most 64 per round are
+                // copied from the pinned host ring into the device ring (the
+                // host appends only while no emitter of the stream is alive)
+                if ((int32_t)(host_seen - end) <= 0) {   // nothing known beyond end (emitters may have moved it)
+                    uint32_t he = 0;
+                    if (lane == 0) he = ld_acquire_sys_u32(&P.mbox->host_end[stream]);
+                    host_seen = __shfl_sync(0xffffffffu, he, 0);
+                }
+                if ((int32_t)(host_seen - end) > 0) {
+                    const uint32_t n = min(host_seen - end, 64u);
+                    constexpr uint32_t kRec16 = sizeof(TaskRec) / 16;
+                    const uint4 *hsrc = reinterpret_cast<const uint4 *>(P.host_recs + (size_t)stream * C);
+                    uint4 *dst = reinterpret_cast<uint4 *>(P.recs + (size_t)stream * C);
+                    uint32_t emits = 0;
+                    for (uint32_t i = lane; i < n * kRec16; i += 32) {
+                        const uint32_t rec = i / kRec16, part = i - rec * kRec16;
+                        const size_t at = (size_t)((end + rec) & (C - 1)) * kRec16 + part;
+                        const uint4 v = ld_volatile_v4(hsrc + at);
+                        dst[at] = v;
+                        if (part == 0 && (v.y & 0xffffu) == ACS_OP_RL_EMIT) ++emits;
+                    }
+                    emits = __reduce_add_sync(0xffffffffu, emits);
+                    // each host-submitted emit task starts one emitter chain
+                    if (lane == 0 && emits) atomicAdd(&P.sctl[stream].open, emits);
+                    __syncwarp();
+                    __threadfence();                   // records and chains before the new end
+                    end += n;
+                    if (lane == 0) {
+                        st_relaxed_u32(&P.sctl[stream].end, end);
+                        sts_volatile(&S.sh->end, end);
+                    }
+                    __syncwarp();
+                    tw = 0;
+                    backoff = 32;
+                    continue;
+                }
+            }
             // an open stream grows when an emitter publishes a larger end
             const uint32_t e = ld_relaxed_u32(&P.sctl[stream].end);
             if ((int32_t)(e - end) > 0) {
@@ -196,6 +258,7 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                 continue;
             }
             wait = true;
+            host_wait = P.resident;                // idle until the host publishes work
         } else {
             const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
             const uint32_t nx = lds_volatile(&S.sh->next);
@@ -219,6 +282,14 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
         }
         if (wait) {
             if (lds_volatile(&S.sh->quit)) return;
+            if (host_wait) {
+                // waiting for the host is not a stall: the scheduler warp bounds
+                // it (idle limit) and raises quit; poll the bus every ~2 us
+                tw = 0;
+                __nanosleep(backoff);
+                if (backoff < 2048) backoff <<= 1;
+                continue;
+            }
             if ((++spins & 63) == 0) {
                 const unsigned long long now = globaltimer_ns();
                 if (tw == 0) tw = now;
@@ -273,7 +344,8 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     const uint32_t first = P.first[stream], end = P.end[stream];
-    const bool open = P.open[stream] != 0;         // then tasks beyond `end` may still come
+    // open or resident: tasks beyond `end` may still come
+    const bool open = P.open[stream] != 0 || P.resident != 0;
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
     constexpr uint32_t kCheckers = kBlock / 32 - 3;   // warps 1 .. 5
@@ -292,7 +364,9 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
                 if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
                 return;
             }
-            if ((++spins & 63) == 0) {
+            // a resident stream waits for the host without bound here; the
+            // scheduler warp's idle limit ends the wait through quit
+            if (!P.resident && (++spins & 63) == 0) {
                 const unsigned long long now = globaltimer_ns();
                 if (tw == 0) tw = now;
                 else if (now - tw > 4ull * P.timeout_ns) {
@@ -360,7 +434,7 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->next = first;
         S.sh->quit = 0;
         S.sh->end = P.end[stream];
-        if (P.open[stream]) {   // published before any emitter of this launch can run
+        if (P.open[stream] || P.resident) {   // published before any emitter of this launch can run
             StreamCtl *sc = &P.sctl[stream];
             sc->end = P.end[stream];
             sc->open = P.open[stream];
@@ -375,7 +449,8 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const uint32_t W = P.window;
     const uint32_t C = 1u << P.cap_log2;
     const uint32_t first = P.first[stream];
-    const bool open = P.open[stream] != 0;
+    const bool resident = P.resident != 0;
+    const bool open = P.open[stream] != 0 || resident;
     uint32_t end = P.end[stream];              // grows while the stream is open
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
@@ -407,6 +482,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
 #define ACS_PHASE(k) do { if (tracing) { const unsigned long long _t = clock64(); ph[k] += _t - tp; tp = _t; } } while (0)
 
     uint32_t head_pub = first;
+    // resident launches: progress reported to the host, idle bookkeeping
+    uint32_t head_host = first, idle_pub = first - 1u, idle_polls = 0;
+    unsigned long long last_hb = 0, hb_time = 0;
     while (first < end || open) {
         bool progress = false;
         const unsigned long long t0 = tracing ? clock64() : 0ull;
@@ -585,6 +663,11 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             st_relaxed_u32(&P.sctl[stream].head_pub, head);
         }
         head_pub = head;
+        if (resident && head - head_host >= 16u && lane == 0) {   // the host's ring-space check
+            st_relaxed_sys_u32(&P.mbox->progress[stream].head, head);
+            head_host = head;
+        }
+        bool idle = false;
         if (head == end) {
             if (!open) { if (tracing) busy += clock64() - t0; break; }
             // open stream: finished once no emitter is left and nothing was appended
@@ -593,7 +676,37 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                 fence_acq_rel_gpu();
                 fin = ld_relaxed_u32(&P.sctl[stream].end) == end;
             }
-            if (__shfl_sync(0xffffffffu, fin, 0)) { if (tracing) busy += clock64() - t0; break; }
+            fin = __shfl_sync(0xffffffffu, fin, 0);
+            if (fin && !resident) { if (tracing) busy += clock64() - t0; break; }
+            if (fin) {
+                // resident and idle: every task below end retired. Tell the host
+                // (its results are visible system-wide first), then look for
+                // the host's drain request or its absence, every 8th idle pass.
+                idle = true;
+                uint32_t leave = 0;
+                if (lane == 0) {
+                    if (end != idle_pub) {
+                        __threadfence_system();
+                        st_relaxed_sys_u32(&P.mbox->progress[stream].head, head);
+                        st_relaxed_sys_u32(&P.mbox->progress[stream].idle_at, end);
+                        idle_pub = end;
+                        head_host = head;
+                    }
+                    if ((++idle_polls & 7) == 0) {
+                        const unsigned long long now = globaltimer_ns();
+                        const unsigned long long hb = ld_relaxed_sys_u64(&P.mbox->heartbeat);
+                        if (hb != last_hb || hb_time == 0) { last_hb = hb; hb_time = now; }
+                        if (ld_acquire_sys_u32(&P.mbox->drain) &&
+                            ld_acquire_sys_u32(&P.mbox->host_end[stream]) == end) {
+                            leave = 1;
+                        } else if (now - hb_time > P.idle_limit_ns) {
+                            st_relaxed_sys_u32(&P.mbox->expired, 1u);
+                            leave = 1;
+                        }
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, leave, 0)) { if (tracing) busy += clock64() - t0; break; }
+            }
         }
 
         ACS_PHASE(7);
@@ -606,6 +719,10 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         if (progress) {
             if (tracing) busy += clock64() - t0;
             idle_since = 0;
+        } else if (idle) {
+            // resident and waiting for the host: bounded by the idle limit above
+            idle_since = 0;
+            __nanosleep(1000);
         } else {
             const unsigned long long now = globaltimer_ns();
             if (idle_since == 0) idle_since = now;
@@ -818,7 +935,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     if (stopped(P)) { quit = 1; break; }
                     const unsigned long long now = globaltimer_ns();
                     if (tw == 0) tw = now;
-                    else if (now - tw > 4ull * P.timeout_ns) {  // idle workers outwait the scheduler's bound
+                    else if (now - tw > 4ull * P.timeout_ns + (P.resident ? P.idle_limit_ns : 0ull)) {
+                        // idle workers outwait the schedulers' bounds
                         raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
                         quit = 1;
                         break;

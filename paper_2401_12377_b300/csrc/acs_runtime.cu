@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "acs_internal.h"
@@ -38,6 +39,8 @@ struct StreamState {
     uint32_t emit_pending = 0;  // emit tasks submitted since the last flush
     bool emitting = false;      // flushed emit tasks not yet synced: the device owns the end
 };
+
+int64_t wrap_diff(uint32_t a, uint32_t b) { return (int64_t)(int32_t)(a - b); }
 
 struct TimedLaunch {
     cudaEvent_t a, b;
@@ -69,6 +72,12 @@ struct acs_ctx {
     unsigned long long *d_trace = nullptr;
     StreamCtl *d_sctl = nullptr;
     HostStatus *h_status = nullptr, *d_status = nullptr;
+    // resident launches (acs_start .. acs_stop)
+    bool resident = false;
+    Mailbox *h_mbox = nullptr, *d_mbox = nullptr;
+    TaskRec *d_hring = nullptr;          // device view of h_ring
+    cudaStream_t side = nullptr;         // abort copies while the resident kernel runs
+    uint32_t *h_one = nullptr;           // pinned source of those copies
     std::vector<StreamState> st;
     int err = ACS_OK;
     uint32_t grid = 0, cta_slots = 0, smem = 0;
@@ -180,10 +189,7 @@ int copy_new_descriptors(acs_ctx *c) {
     return ACS_OK;
 }
 
-int flush_window(acs_ctx *c) {
-    int rc = copy_new_descriptors(c);
-    if (rc) return rc;
-    KParams P;
+void fill_params(acs_ctx *c, KParams &P) {
     std::memset(&P, 0, sizeof P);
     P.recs = c->d_ring;
     P.ctl = c->d_ctl;
@@ -207,11 +213,12 @@ int flush_window(acs_ctx *c) {
     P.flags = c->cfg.flags;
     P.sched_smem = sched_smem_bytes(c->W);
     P.poll_ns = c->cfg.poll_ns ? c->cfg.poll_ns : 128u;
-    for (uint32_t s = 0; s < c->S; ++s) {
-        P.first[s] = c->st[s].flushed;
-        P.end[s] = c->st[s].submitted;
-        P.open[s] = (uint8_t)std::min<uint32_t>(c->st[s].emit_pending, 255u);
-    }
+    P.mbox = c->d_mbox;
+    P.host_recs = c->d_hring;
+    P.idle_limit_ns = (unsigned long long)(c->cfg.idle_limit_ms ? c->cfg.idle_limit_ms : 10000u) * 1000000ull;
+}
+
+int launch_persistent(acs_ctx *c, KParams &P) {
     void *args[] = {&P};
     TimedLaunch t{};
     const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
@@ -230,6 +237,64 @@ int flush_window(acs_ctx *c) {
         c->timed.push_back(t);
     }
     c->stats.launches++;
+    return ACS_OK;
+}
+
+int flush_window(acs_ctx *c) {
+    int rc = copy_new_descriptors(c);
+    if (rc) return rc;
+    KParams P;
+    fill_params(c, P);
+    for (uint32_t s = 0; s < c->S; ++s) {
+        P.first[s] = c->st[s].flushed;
+        P.end[s] = c->st[s].submitted;
+        P.open[s] = (uint8_t)std::min<uint32_t>(c->st[s].emit_pending, 255u);
+    }
+    return launch_persistent(c, P);
+}
+
+// ---- resident launches ---------------------------------------------------------------
+
+void heartbeat(acs_ctx *c) {
+    __atomic_fetch_add(&c->h_mbox->heartbeat, 1ull, __ATOMIC_RELAXED);
+}
+
+// Take in what the device reported for stream s: released tasks free ring
+// space; an idle end at or past everything published means the stream's
+// tasks (and any emitter chain they started) all retired.
+void refresh_stream(acs_ctx *c, uint32_t s) {
+    StreamState &ss = c->st[s];
+    const uint32_t head = __atomic_load_n(&c->h_mbox->progress[s].head, __ATOMIC_ACQUIRE);
+    const uint32_t idle = __atomic_load_n(&c->h_mbox->progress[s].idle_at, __ATOMIC_ACQUIRE);
+    if (wrap_diff(head, ss.synced) > 0 && wrap_diff(head, ss.flushed) <= 0) ss.synced = head;
+    if (wrap_diff(idle, ss.flushed) >= 0) {
+        if (ss.emitting) {   // the chain's final end: the stream continues after it
+            c->stats.tasks_emitted += idle - ss.flushed;
+            ss.submitted = ss.flushed = idle;
+            if (idle) { ss.has_id = true; ss.last_id = std::max(ss.last_id, idle - 1); }
+            ss.emitting = false;
+        }
+        ss.synced = ss.flushed;
+    }
+}
+
+int resident_status(acs_ctx *c) {
+    const uint32_t e = __atomic_load_n(&c->h_mbox->err, __ATOMIC_ACQUIRE);
+    if (e) return fail(c, (int)(int32_t)e);
+    if (__atomic_load_n(&c->h_mbox->expired, __ATOMIC_ACQUIRE)) return fail(c, ACS_ERR_STOPPED);
+    return ACS_OK;
+}
+
+int flush_resident(acs_ctx *c) {
+    int rc = resident_status(c);
+    if (rc) return rc;
+    for (uint32_t s = 0; s < c->S; ++s) {
+        StreamState &ss = c->st[s];
+        if (ss.submitted == ss.flushed) continue;
+        // the descriptors are in the pinned ring; this store publishes them
+        __atomic_store_n(&c->h_mbox->host_end[s], ss.submitted, __ATOMIC_RELEASE);
+    }
+    heartbeat(c);
     return ACS_OK;
 }
 
@@ -388,6 +453,7 @@ int acs_error(const acs_ctx *ctx) { return ctx ? ctx->err : ACS_ERR_INVALID; }
 
 void acs_destroy(acs_ctx *c) {
     if (!c) return;
+    if (c->resident) acs_stop(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     release_graphs(c, false);
     for (auto &t : c->timed) c->event_pool.push_back(t);
@@ -409,6 +475,9 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_sctl);
     if (c->h_ring) cudaFreeHost(c->h_ring);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_mbox) cudaFreeHost(c->h_mbox);
+    if (c->h_one) cudaFreeHost(c->h_one);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -465,7 +534,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
         c->own_stream = true;
     }
     const size_t nrec = (size_t)c->S * c->C;
-    chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocDefault));
+    chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocMapped));
     chk(cudaMalloc(&c->d_ring, nrec * sizeof(TaskRec)));
     chk(cudaMalloc(&c->d_ctl, sizeof(DevCtl)));
     const uint32_t nslots = c->S * kMaxWindow;
@@ -487,9 +556,15 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMalloc(&c->d_sched_stats, c->S * sizeof(SchedStats)));
     chk(cudaMalloc(&c->d_sctl, c->S * sizeof(StreamCtl)));
     chk(cudaHostAlloc(&c->h_status, sizeof(HostStatus), cudaHostAllocMapped));
+    chk(cudaHostAlloc(&c->h_mbox, sizeof(Mailbox), cudaHostAllocMapped));
+    chk(cudaHostAlloc(&c->h_one, sizeof(uint32_t), cudaHostAllocDefault));
     if (rc) { acs_destroy(c); return rc; }
     std::memset((void *)c->h_status, 0, sizeof(HostStatus));
+    std::memset((void *)c->h_mbox, 0, sizeof(Mailbox));
+    *c->h_one = 1u;
     chk(cudaHostGetDevicePointer((void **)&c->d_status, (void *)c->h_status, 0));
+    chk(cudaHostGetDevicePointer((void **)&c->d_mbox, (void *)c->h_mbox, 0));
+    chk(cudaHostGetDevicePointer((void **)&c->d_hring, (void *)c->h_ring, 0));
     chk(cudaMemsetAsync(c->d_sched_stats, 0, c->S * sizeof(SchedStats), c->stream));
     chk(cudaMemsetAsync(c->d_sctl, 0, c->S * sizeof(StreamCtl), c->stream));
     chk(cudaMemsetAsync(c->d_log_mask, 0, nlog * sizeof(unsigned long long), c->stream));
@@ -612,6 +687,8 @@ int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_a
     if (!args || stream >= c->S || (n_reads && !reads) || (n_writes && !writes)) return ACS_ERR_INVALID;
     if (!valid_op(args->op) || args->ncta < 1 || args->ncta > ACS_MAX_NCTA || args->reserved) return ACS_ERR_INVALID;
     StreamState &ss = c->st[stream];
+    const bool full = (uint64_t)ss.submitted + c->W - 1 - ss.synced + 1 > c->C - kPrefetch;
+    if (c->resident && (ss.emitting || full)) refresh_stream(c, stream);
     if (ss.emitting) return ACS_ERR_INVALID;   // sync first: the device appends to this stream
     if (args->op == ACS_OP_RL_EMIT && c->cfg.mode != ACS_MODE_WINDOW) return ACS_ERR_INVALID;
     if (ss.has_id && task_id <= ss.last_id) return ACS_ERR_ORDER;
@@ -667,7 +744,8 @@ int acs_flush(acs_ctx *c) {
     for (auto &s : c->st) n += s.submitted - s.flushed;
     if (!n) return ACS_OK;
     int rc;
-    if (c->cfg.mode == ACS_MODE_WINDOW) rc = flush_window(c);
+    if (c->resident) rc = flush_resident(c);
+    else if (c->cfg.mode == ACS_MODE_WINDOW) rc = flush_window(c);
     else if (c->cfg.mode == ACS_MODE_INORDER) rc = flush_inorder(c);
     else rc = flush_graph(c);
     if (rc) return rc;
@@ -680,8 +758,41 @@ int acs_flush(acs_ctx *c) {
     return ACS_OK;
 }
 
+// Resident: wait on the host, without ending the kernel, until every
+// published task (and the emitter chains they started) retired.
+int sync_resident(acs_ctx *c) {
+    using clk = std::chrono::steady_clock;
+    auto last = clk::now();
+    std::vector<uint32_t> seen(c->S, 0);
+    while (true) {
+        int rc = resident_status(c);
+        if (rc) return rc;
+        bool all = true, moved = false;
+        for (uint32_t s = 0; s < c->S; ++s) {
+            refresh_stream(c, s);
+            const StreamState &ss = c->st[s];
+            const uint32_t h = __atomic_load_n(&c->h_mbox->progress[s].head, __ATOMIC_RELAXED);
+            if (h != seen[s]) { seen[s] = h; moved = true; }
+            if (ss.emitting || ss.synced != ss.flushed) all = false;
+        }
+        if (all) return ACS_OK;
+        heartbeat(c);
+        const cudaError_t q = cudaStreamQuery(c->stream);
+        if (q != cudaErrorNotReady) {     // the kernel is gone before the work retired
+            return q == cudaSuccess ? fail(c, ACS_ERR_STOPPED) : cuda_fail(c, q);
+        }
+        const auto now = clk::now();
+        if (moved) last = now;
+        else if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - last).count() >
+                 c->cfg.timeout_ns)
+            return fail(c, ACS_ERR_TIMEOUT);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
 int acs_sync(acs_ctx *c) {
     if (!c) return ACS_ERR_INVALID;
+    if (c->resident) return sync_resident(c);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     collect_timing(c);
@@ -769,6 +880,115 @@ int acs_get_trace(acs_ctx *c, uint32_t stream, uint64_t first, uint32_t n, uint6
         done += m;
     }
     return ACS_OK;
+}
+
+int acs_start(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    if (c->cfg.mode != ACS_MODE_WINDOW || c->resident) return ACS_ERR_INVALID;
+    for (auto &s : c->st)
+        if (s.flushed != s.synced || s.emitting) return ACS_ERR_INVALID;   // acs_sync first
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    collect_timing(c);
+    Mailbox *m = c->h_mbox;
+    std::memset((void *)m, 0, sizeof(Mailbox));
+    for (uint32_t s = 0; s < c->S; ++s) {
+        m->host_end[s] = c->st[s].flushed;
+        m->progress[s].head = m->progress[s].idle_at = c->st[s].flushed;
+    }
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    KParams P;
+    fill_params(c, P);
+    P.resident = 1;
+    for (uint32_t s = 0; s < c->S; ++s) {
+        P.first[s] = c->st[s].flushed;
+        P.end[s] = c->st[s].flushed;
+        P.open[s] = 0;
+    }
+    int rc = launch_persistent(c, P);
+    if (rc) return rc;
+    c->resident = true;
+    // tasks submitted before the start are published now
+    return acs_flush(c);
+}
+
+int acs_progress(acs_ctx *c, uint32_t *head, uint32_t *idle_at) {
+    if (!c) return ACS_ERR_INVALID;
+    if (!c->resident) {   // what the last acs_sync established
+        for (uint32_t s = 0; s < c->S; ++s) {
+            if (head) head[s] = c->st[s].synced;
+            if (idle_at) idle_at[s] = c->st[s].synced;
+        }
+        return c->err;
+    }
+    heartbeat(c);
+    for (uint32_t s = 0; s < c->S; ++s) {
+        refresh_stream(c, s);
+        if (head) head[s] = __atomic_load_n(&c->h_mbox->progress[s].head, __ATOMIC_ACQUIRE);
+        if (idle_at) idle_at[s] = __atomic_load_n(&c->h_mbox->progress[s].idle_at, __ATOMIC_ACQUIRE);
+    }
+    return resident_status(c);
+}
+
+int acs_stop(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    if (!c->resident) return c->err;
+    using clk = std::chrono::steady_clock;
+    // publish what is staged, then ask every scheduler to leave once idle
+    if (!c->err) acs_flush(c);
+    __atomic_store_n(&c->h_mbox->drain, 1u, __ATOMIC_RELEASE);
+    heartbeat(c);
+    auto last = clk::now();
+    std::vector<uint32_t> seen(c->S, 0);
+    bool aborted = false;
+    while (true) {
+        const cudaError_t q = cudaStreamQuery(c->stream);
+        if (q != cudaErrorNotReady) break;
+        bool moved = false;
+        for (uint32_t s = 0; s < c->S; ++s) {
+            const uint32_t h = __atomic_load_n(&c->h_mbox->progress[s].head, __ATOMIC_RELAXED);
+            if (h != seen[s]) { seen[s] = h; moved = true; }
+        }
+        const auto now = clk::now();
+        if (moved) last = now;
+        const uint64_t still = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - last).count();
+        if (!aborted && (c->err || still > c->cfg.timeout_ns)) {
+            // no progress: raise the device stop flag through a copy that runs
+            // beside the kernel; every device wait then ends
+            if (!c->side) cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+            if (c->side) {
+                cudaMemcpyAsync(&c->d_ctl->stop, c->h_one, sizeof(uint32_t), cudaMemcpyHostToDevice, c->side);
+                cudaStreamSynchronize(c->side);
+            }
+            if (!c->err) fail(c, ACS_ERR_TIMEOUT);
+            aborted = true;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    c->resident = false;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    collect_timing(c);
+    const uint32_t derr = c->h_status->err;
+    if (derr) fail(c, (int)(int32_t)derr);
+    // final ends of every stream, emitter chains included
+    std::vector<StreamCtl> sc(c->S);
+    e = cudaMemcpy(sc.data(), c->d_sctl, c->S * sizeof(StreamCtl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    for (uint32_t i = 0; i < c->S; ++i) {
+        StreamState &s = c->st[i];
+        if (s.emitting && !c->err) {
+            c->stats.tasks_emitted += sc[i].end - s.flushed;
+            s.submitted = s.flushed = sc[i].end;
+            if (sc[i].end) { s.has_id = true; s.last_id = std::max(s.last_id, sc[i].end - 1); }
+        }
+        s.emitting = false;
+        s.emit_pending = 0;
+        if (!c->err) s.synced = s.flushed;
+    }
+    if (!c->err && __atomic_load_n(&c->h_mbox->expired, __ATOMIC_ACQUIRE)) return ACS_ERR_STOPPED;
+    return c->err;
 }
 
 int acs_stream_tail(acs_ctx *c, uint32_t stream, uint32_t *tail) {

@@ -58,7 +58,8 @@ class DeviceBuffers:
             self.t[k].copy_(torch.from_numpy(np.ascontiguousarray(v).view(np.uint8)))
 
     def download(self) -> Dict[str, np.ndarray]:
-        torch.cuda.synchronize()
+        # the current stream only: a resident scheduler kernel keeps the device busy
+        torch.cuda.current_stream().synchronize()
         return {k: v.cpu().numpy().view(self.dtype[k]) for k, v in self.t.items()}
 
 
@@ -128,7 +129,7 @@ class Context:
     def __init__(self, window: int, mode: str = "window", n_streams: int = 1, cta_slots: int = 0,
                  capacity: int = 0, log: bool = False, timing: bool = False, trace: bool = False,
                  timeout_s: float = 5.0, poll_ns: int = 0, ctas_per_sm: int = 0,
-                 cuda_stream: Optional[int] = None):
+                 cuda_stream: Optional[int] = None, resident: bool = False, idle_limit_ms: int = 0):
         cfg = acs.acs_config_default()
         cfg.mode = MODES[mode]
         cfg.n_streams = n_streams
@@ -140,11 +141,22 @@ class Context:
         cfg.timeout_ns = int(timeout_s * 1e9)
         cfg.poll_ns = poll_ns
         cfg.ctas_per_sm = ctas_per_sm
+        cfg.idle_limit_ms = idle_limit_ms
         # All device work of the context goes to one stream shared with torch, so
         # torch copies of the task buffers are ordered with the tasks. The legacy
         # default stream has no handle to share: then a torch stream is made
         # current for the context's lifetime.
         self._prev_stream = None
+        self._lib_stream = None
+        if cuda_stream is None and resident:
+            # a resident kernel occupies its stream until stopped: the library
+            # gets a stream of its own, torch's current stream stays free for
+            # the caller's copies (which the caller completes before flushing)
+            if torch.cuda.current_stream().cuda_stream == 0:
+                self._prev_stream = torch.cuda.current_stream()
+                torch.cuda.set_stream(torch.cuda.Stream())
+            self._lib_stream = torch.cuda.Stream()
+            cuda_stream = self._lib_stream.cuda_stream
         if cuda_stream is None:
             cur = torch.cuda.current_stream()
             if cur.cuda_stream == 0:
@@ -157,6 +169,23 @@ class Context:
         cfg.cuda_stream = C.c_void_p(cuda_stream)
         self.window, self.mode, self.n_streams = window, mode, n_streams
         self.h = acs.acs_init(window, cfg)
+        self.resident = False
+        if resident:
+            self.start()
+
+    def start(self) -> None:
+        """Leave the scheduler kernel resident (acs_start)."""
+        acs.acs_start(self.h)
+        self.resident = True
+
+    def stop(self) -> None:
+        """Drain and end the resident kernel (acs_stop)."""
+        self.resident = False
+        acs.acs_stop(self.h)
+
+    def progress(self, head: Optional[np.ndarray] = None, idle_at: Optional[np.ndarray] = None):
+        """(head, idle_at) per stream (acs_progress)."""
+        return acs.acs_progress(self.h, self.n_streams, head, idle_at)
 
     def submit_packed(self, ids: np.ndarray, packed: np.ndarray, stream: int = 0) -> None:
         acs.check(acs.acs_submit_ops(self.h, stream, ids, packed), "acs_submit_ops")
