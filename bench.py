@@ -36,11 +36,15 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
+WORKLOAD_SERVING = ("serving: Poisson arrivals of rigid-sphere (64 envs, device-side emission) / gated-MLP "
+                    "(batch 1-8, shared weights) requests of 100-5000 tasks, 20 GB budget, resident kernel")
 WORKLOAD_BATCHED = ("batched: 64 independent streams (alternating rigid-sphere 64 envs x 32 spheres / gated "
                     "residual MLP hidden 256, batch 1-8), lengths log-uniform in [100, 5000] tasks, one launch")
 
@@ -51,8 +55,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["acs", "reference"], default="acs")
-    ap.add_argument("--workload", choices=["rlsim", "batched"], default="rlsim",
-                    help="rlsim: one rigid-sphere stream (default); batched: 64 independent streams in one launch")
+    ap.add_argument("--workload", choices=["rlsim", "batched", "serving"], default="rlsim",
+                    help="rlsim: one rigid-sphere stream (default); batched: 64 independent streams in one "
+                         "launch; serving: Poisson arrivals over a resident kernel (steps = seconds of arrivals)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=64, help="serving: stream slots (concurrent requests)")
     ap.add_argument("--window", type=int, default=0, help="window size (default: 32, or autotuned for batched)")
     ap.add_argument("--cta-slots", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
@@ -109,6 +116,34 @@ def oracle_batch(seed: int, limit_s: float = 1e9):
     return tasks, streams, time.perf_counter() - t0
 
 
+def oracle_serving(seed: int, n_req: int, rate: float, limit_s: float, offset: int = 0):
+    """The oracle over serving requests in arrival order (from request
+    offset * 97), stopping after the request that crosses limit_s; returns
+    (tasks, requests, s)."""
+    import streamgen as sg
+    from oracle import execute
+    execute.build_c()
+    cat = sg.serving_catalogue(seed)
+    shared = sg.dnn_weights(1234, sg.DNN_SERVE_WEIGHT_SETS)
+    _, kinds = sg.poisson_arrivals(seed, n_req, rate, len(cat))
+    tasks = reqs = 0
+    t0 = time.perf_counter()
+    for i in range(len(kinds)):
+        sp = cat[int(kinds[(i + offset * 97) % len(kinds)])]
+        if sp.kind == "rl":
+            t, _, _ = execute.run_rlsim(sg.RLSim(sp.seed, sp.rl), emit=True)
+        else:
+            st = sg.dnn_stream(sp.seed, batch=sp.dnn_batch, blocks=sp.dnn_blocks,
+                               weight_sets=sg.DNN_SERVE_WEIGHT_SETS, shared=shared)
+            execute.run_inorder(st.buffers, st.tasks)
+            t = st.tasks
+        tasks += len(t)
+        reqs += 1
+        if time.perf_counter() - t0 > limit_s:
+            break
+    return tasks, reqs, time.perf_counter() - t0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -116,6 +151,25 @@ def run_reference(args):
     import streamgen as sg
     from oracle import execute
     execute.build_c()
+    if args.workload == "serving":
+        n_req = int(args.rate * args.steps)
+        times, tasks = [], 0
+        for k in range(args.steps):
+            t, _, dt = oracle_serving(1, n_req, args.rate, limit_s=20.0, offset=k)
+            times.append(dt)
+            tasks += t
+        s_tot = sum(times)
+        value = tasks / s_tot
+        line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": 0, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD_SERVING, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"requests in arrival order, about 20 s of in-order execution per step "
+                                           f"({tasks} tasks in all), single-threaded"},
+                "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "batched":
         oracle_batch(100)   # warm-up: imports, compiled bodies
         times, tasks = [], 0
@@ -461,6 +515,86 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     return line
 
 
+def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
+    """Open-loop serving: requests arrive as a Poisson process (args.rate per
+    second, args.steps seconds of arrivals after args.warmup x 100 warm-up
+    requests) and are served by one resident kernel with args.slots stream
+    slots and a 20 GB budget. Host clock throughout: latency is completion seen
+    by the host minus arrival; every request's inputs go host to device and its
+    results device to host inside the run."""
+    import streamgen as sg
+    from paper_2401_12377_b300 import harness, serving
+    seed = 1 + rank
+    t_prep = time.perf_counter()
+    specs = sg.serving_catalogue(seed)
+    cat = serving.Catalogue(specs)
+    t_prep = time.perf_counter() - t_prep
+    W = args.window or 32
+    n_req = int(round(args.rate * args.steps))
+    arrivals, kinds = sg.poisson_arrivals(seed, n_req, args.rate, len(specs))
+    wa, wk = sg.poisson_arrivals(seed + 1000, max(1, 100 * args.warmup), args.rate, len(specs))
+    ctx = harness.Context(W, n_streams=args.slots, resident=True, timing=True, capacity=1 << 13)
+    srv = serving.Server(cat, ctx, budget_bytes=20 << 30, readback=True)
+    srv.run(wa, wk)
+    if dist:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        r = srv.run(arrivals, kinds)
+    clocks = clk.summary()
+    ctx.stop()
+    st = ctx.stats()
+    ctx.close()
+    lat = np.sort(r["latency_s"]) * 1e3
+    q = np.sort(r["queue_s"]) * 1e3
+    tasks = int(r["tasks"].sum())
+    span = r["span_s"]
+    tps = r["tasks_per_s"]
+    if dist:
+        t = torch.tensor([span], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        span = float(t.item())
+    value = world * tasks / span
+    pct = lambda a, p: float(a[min(len(a) - 1, int(p * len(a)))])
+    mean_len = float(np.mean([specs[int(k)].target for k in kinds]))
+    kernel_s = st["kernel_ms"] / 1e3
+    line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_SERVING, "requests": n_req, "rate_per_s": args.rate,
+                       "step": "one second of arrivals", "slots": args.slots, "window": W, "budget_gb": 20,
+                       "catalogue_types": len(specs), "mean_request_tasks": mean_len,
+                       "timing": "host clock (perf_counter) from first arrival to last completion",
+                       "l2": "not flushed: a continuous open-loop run over > 126 MB of request data",
+                       "parallelism": f"independent servers x{world}" if world > 1 else "one GPU"},
+            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": float(lat.mean()),
+                           "max": float(lat[-1])},
+            "queue_wait_ms": {"p50": pct(q, 0.5), "p99": pct(q, 0.99)},
+            "offered_tasks_per_s": args.rate * mean_len,
+            "mean_in_flight": r["mean_in_flight"], "peak_device_bytes": r["peak_bytes"],
+            "requests_per_s": n_req / span,
+            "resident_kernel_s": kernel_s, "catalogue_prep_s": t_prep,
+            "roofline": {"bound": "hbm", "achieved": st["device_seg_bytes"] / kernel_s / 1e9 if kernel_s else 0.0,
+                         "peak": float(peaks.get("hbm_gbs", 6400.0)), "unit": "GB/s",
+                         "frac": (st["device_seg_bytes"] / kernel_s / 1e9 if kernel_s else 0.0)
+                         / float(peaks.get("hbm_gbs", 6400.0)),
+                         "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
+                         "note": "segment bytes of all tasks over the resident launch's whole life "
+                                 "(warm-up, timed run and idle gaps included): a utilisation figure"},
+            "gpu_launches": int(st["launches"]),
+            "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": int(r["h2d_bytes"] / args.steps),
+                    "d2h_bytes_per_step": int(r["d2h_bytes"] / args.steps),
+                    "note": "the serving loop is end to end: inputs uploaded and results read back per request"},
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t, nr, dt = oracle_serving(seed, n_req, args.rate, limit_s=10.0)
+        line["cpu_baseline"] = {"value": t / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {nr} requests in arrival order ({t} tasks), "
+                                          f"single-threaded numpy + C bodies, {dt:.1f} s"}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -492,8 +626,11 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream())
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     seed = 1 + rank
-    if args.workload == "batched":
-        line = bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
+    if args.workload in ("batched", "serving"):
+        if args.workload == "batched":
+            line = bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
+        else:
+            line = bench_serving(args, torch, dist, world, rank, peaks, peak_src)
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist:

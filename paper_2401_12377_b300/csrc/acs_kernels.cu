@@ -696,8 +696,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                         const unsigned long long now = globaltimer_ns();
                         const unsigned long long hb = ld_relaxed_sys_u64(&P.mbox->heartbeat);
                         if (hb != last_hb || hb_time == 0) { last_hb = hb; hb_time = now; }
+                        // (emitters may have taken the end past the host's)
                         if (ld_acquire_sys_u32(&P.mbox->drain) &&
-                            ld_acquire_sys_u32(&P.mbox->host_end[stream]) == end) {
+                            (int32_t)(ld_acquire_sys_u32(&P.mbox->host_end[stream]) - end) <= 0) {
                             leave = 1;
                         } else if (now - hb_time > P.idle_limit_ns) {
                             st_relaxed_sys_u32(&P.mbox->expired, 1u);

@@ -133,8 +133,17 @@ def dnn_gate(seed: int, sample: int, block: int) -> int:
     return int((mix(seed, 0xD5, sample, block) >> 17) & 1)
 
 
+def dnn_weights(seed: int, sets: int = 24, hidden: int = 256):
+    """(W, B): ``sets`` weight sets of the gated MLP, U[-1/16, 1/16), shaped as
+    dnn_stream lays them out (flat float32)."""
+    rng = np.random.default_rng(seed)
+    W = rng.uniform(-1.0 / 16, 1.0 / 16, (sets, 2, hidden, hidden)).astype(np.float32)
+    B = rng.uniform(-1.0 / 16, 1.0 / 16, (sets, 2, hidden)).astype(np.float32)
+    return W.reshape(-1), B.reshape(-1)
+
+
 def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
-               window: int = 32, task_id0: int = 0, weight_sets: int = 0) -> Stream:
+               window: int = 32, task_id0: int = 0, weight_sets: int = 0, shared=None) -> Stream:
     """Gated residual MLP inference for ``batch`` samples, in block-major order.
 
     Block k of sample s runs iff ``dnn_gate(seed, s, k)``; a run block is four
@@ -144,12 +153,19 @@ def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
     samples' chains are independent; weights are shared read-only. GEMV tasks
     use 1..32 CTAs (seeded), the elementwise ones 1 CTA. With ``weight_sets``
     > 0 block k uses weight set k mod weight_sets (long streams, bounded memory).
+    ``shared`` = (W, B) from dnn_weights (weight_sets of them) replaces the
+    stream's own weights (many requests serving one model); the inputs then
+    come from the seed alone.
     """
     rng = np.random.default_rng(seed)
     H = hidden
     nw = weight_sets if weight_sets > 0 else blocks
-    W = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H, H)).astype(np.float32)
-    B = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H)).astype(np.float32)
+    if shared is None:
+        W = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H, H)).astype(np.float32)
+        B = rng.uniform(-1.0 / 16, 1.0 / 16, (nw, 2, H)).astype(np.float32)
+    else:
+        W, B = shared
+        assert W.size == nw * 2 * H * H and B.size == nw * 2 * H
     h = rng.uniform(-1.0, 1.0, (batch, H)).astype(np.float32)
     bufs = {"W": W.reshape(-1), "B": B.reshape(-1), "h": h.reshape(-1),
             "t": np.zeros(batch * H, np.float32), "u": np.zeros(batch * H, np.float32)}
@@ -426,3 +442,39 @@ def batched_specs(seed: int, n_streams: int = 64, lo: int = 100, hi: int = 5000)
             blocks = max(1, int(round(L / (2 * b))))      # ~4 tasks per sample for half the blocks
             out.append(BatchSpec("dnn", sseed, L, dnn_batch=b, dnn_blocks=blocks))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Serving: Poisson arrivals of requests drawn from a catalogue of streams
+# ----------------------------------------------------------------------------
+
+DNN_SERVE_BATCHES = (1, 2, 4, 8)
+DNN_SERVE_WEIGHT_SETS = 24
+
+
+def serving_catalogue(seed: int, n_types: int = 256, lo: int = 100, hi: int = 5000) -> List[BatchSpec]:
+    """Request types: half rigid-sphere runs (64 environments, device-side
+    emission), half gated-MLP inferences (batch in {1, 2, 4, 8}, the 24 shared
+    weight sets of one model), each of a length log-uniform in [lo, hi]
+    tasks, kinds interleaved."""
+    out = []
+    for i, L in enumerate(loguniform_lengths(mix(seed, 0x5E) & 0xFFFFFFFF, n_types, lo, hi)):
+        sseed = mix(seed, 0x5F, i) & 0xFFFFFFFF
+        if i % 2 == 0:
+            per_step = RL_BATCH_ENVS + 2 * (RL_BATCH_ENVS // 8) + 1
+            steps = max(1, int(round(L / per_step)))
+            out.append(BatchSpec("rl", sseed, L, rl=RLParams(n_env=RL_BATCH_ENVS, steps=steps)))
+        else:
+            b = DNN_SERVE_BATCHES[mix(seed, 0x60, i) % len(DNN_SERVE_BATCHES)]
+            blocks = max(1, int(round(L / (2 * b))))
+            out.append(BatchSpec("dnn", sseed, L, dnn_batch=b, dnn_blocks=blocks))
+    return out
+
+
+def poisson_arrivals(seed: int, n: int, rate: float, n_types: int):
+    """(arrival times in s, catalogue index) of n requests: exponential gaps of
+    mean 1/rate, request types uniform over the catalogue."""
+    rng = np.random.default_rng(mix(seed, 0x61) & 0xFFFFFFFF)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    kinds = rng.integers(0, n_types, n)
+    return t, kinds

@@ -252,3 +252,17 @@ def test_release_order_check_accepts_ring_issue_and_rejects_a_violation():
     bad = list(start)
     bad[20] = -1                                # starts before anything retired
     assert deps.check_release_order(bad, retire, 8)
+
+
+def test_serving_arrivals_and_catalogue():
+    """The serving workload's inputs: exponential gaps of mean 1/rate, request
+    kinds half and half, lengths within [lo, hi]."""
+    t, k = sg.poisson_arrivals(1, 20000, 2000.0, 256)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert (gaps > 0).all() and abs(gaps.mean() - 1 / 2000.0) < 0.03 / 2000.0
+    assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.05          # exponential: cv = 1
+    assert k.min() >= 0 and k.max() < 256
+    cat = sg.serving_catalogue(1, n_types=256)
+    assert sum(c.kind == "rl" for c in cat) == 128
+    assert all(100 <= c.target <= 5000 for c in cat)
+    assert {c.dnn_batch for c in cat if c.kind == "dnn"} == {1, 2, 4, 8}
