@@ -68,6 +68,28 @@ def parse():
     return ap.parse_args()
 
 
+def ranks():
+    """(world, rank, local rank) from the launcher's environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank processes the same amount of independent work)."""
+    return world * units_per_rank / max_seconds
+
+
 def rl_params(steps=50):
     import streamgen as sg
     return sg.RLParams(n_env=256, steps=steps)
@@ -428,18 +450,14 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     clocks = clk.summary()
     ms_step = statistics.mean(res["ms"])
     tasks_per_step = res["tasks"] / args.steps
-    max_ms = ms_step
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
+    max_ms = max_over_ranks(ms_step, dist, "cuda")
     st = res["stats"]
     launches = st["launches"]
     avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
     bytes_per_launch = st["device_seg_bytes"] / max(1, launches)
     achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6400.0))
-    line = {"metric": METRIC, "value": world * tasks_per_step / (max_ms / 1e3), "unit": "tasks/s",
+    line = {"metric": METRIC, "value": whole_job_rate(world, tasks_per_step, max_ms / 1e3), "unit": "tasks/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -549,11 +567,8 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
     tasks = int(r["tasks"].sum())
     span = r["span_s"]
     tps = r["tasks_per_s"]
-    if dist:
-        t = torch.tensor([span], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        span = float(t.item())
-    value = world * tasks / span
+    span = max_over_ranks(span, dist, "cuda")
+    value = whole_job_rate(world, tasks, span)
     pct = lambda a, p: float(a[min(len(a) - 1, int(p * len(a)))])
     mean_len = float(np.mean([specs[int(k)].target for k in kinds]))
     kernel_s = st["kernel_ms"] / 1e3
@@ -601,9 +616,7 @@ def main():
         run_reference(args)
         return
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = ranks()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
@@ -649,12 +662,8 @@ def main():
     clocks = clk.summary()
     ms_step = statistics.mean(res["ms"])
     tasks_per_step = res["tasks"] / args.steps
-    max_ms = ms_step
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
-    value = world * tasks_per_step / (max_ms / 1e3)
+    max_ms = max_over_ranks(ms_step, dist, "cuda")
+    value = whole_job_rate(world, tasks_per_step, max_ms / 1e3)
     st = res["stats"]
     launches = st["launches"]
     kernel_ms = st["kernel_ms"]

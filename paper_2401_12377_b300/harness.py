@@ -340,6 +340,7 @@ class RLEmitDriver:
             cfg[k] = sc["rl_integrate"][k]
         self.cfg = torch.from_numpy(cfg.view(np.uint8).copy()).to("cuda")
         self.table = torch.from_numpy(sim.ncta_table()).to("cuda")
+        self._packed = None   # the first tasks' rows: the same every run, ids aside
 
     def first_tasks(self):
         p = self.sim.p
@@ -356,8 +357,12 @@ class RLEmitDriver:
         stream position the run starts at."""
         start = self.ctx.tail(self.stream)
         # emitted tasks take task_id = their position, so ids continue from there
-        self.sim.next_id = start
-        self.ctx.submit(self.first_tasks(), self.bufs, stream=self.stream)
+        if self._packed is None:
+            self.sim.next_id = 0
+            self._packed = pack_tasks(self.first_tasks(), self.bufs)
+        ids, rows = self._packed
+        self.sim.next_id = start + len(ids)
+        self.ctx.submit_packed(ids + np.uint32(start), rows, stream=self.stream)
         return start
 
     def run(self) -> int:
