@@ -19,6 +19,7 @@ Prints ONE JSON line (rank 0). Arms measured on the same box and workload:
   inorder                one kernel launch per task on one stream
   graph_launch           CUDA graph of each batch's full DAG, launch time only
   graph_with_build       same, including host DAG build + instantiate
+  sw_host_scheduler      the paper's software scheduler (host window, 8 threads x 1 stream)
 ``--impl reference`` times the CPU oracle (in-order executor) instead.
 
 Timing: CUDA events on the library's stream around each bench step, L2
@@ -43,6 +44,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
+WORKLOAD_DNN = ("dynamic DNN: gated residual MLP, hidden 256, 24 blocks, shared weights; 100 inputs for each "
+                "batch size 1, 2, 4, 8, one flush (one launch) per input, window 32")
 WORKLOAD_SERVING = ("serving: Poisson arrivals of rigid-sphere (64 envs, device-side emission) / gated-MLP "
                     "(batch 1-8, shared weights) requests of 100-5000 tasks, 20 GB budget, resident kernel")
 WORKLOAD_BATCHED = ("batched: 64 independent streams (alternating rigid-sphere 64 envs x 32 spheres / gated "
@@ -55,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["acs", "reference"], default="acs")
-    ap.add_argument("--workload", choices=["rlsim", "batched", "serving"], default="rlsim",
+    ap.add_argument("--workload", choices=["rlsim", "dnn", "batched", "serving"], default="rlsim",
                     help="rlsim: one rigid-sphere stream (default); batched: 64 independent streams in one "
                          "launch; serving: Poisson arrivals over a resident kernel (steps = seconds of arrivals)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
@@ -173,6 +176,29 @@ def run_reference(args):
     import streamgen as sg
     from oracle import execute
     execute.build_c()
+    if args.workload == "dnn":
+        shared = sg.dnn_weights(7919, 24)
+        streams = [sg.dnn_stream(100000 + b * 1000 + i, batch=b, blocks=24, weight_sets=24, shared=shared)
+                   for b in (1, 2, 4, 8) for i in range(100)]
+        times, tasks = [], 0
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            n = 0
+            for st in streams[k * 7 % 100::25]:      # a bounded sample: 16 inputs of every batch size
+                execute.run_inorder(st.buffers, st.tasks)
+                n += len(st.tasks)
+            times.append(time.perf_counter() - t0)
+            tasks += n
+        value = tasks / sum(times)
+        line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": 0, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD_DNN, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                 "sample": "each step 16 of the 400 inputs (4 of each batch size), single-threaded"},
+                "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "serving":
         n_req = int(args.rate * args.steps)
         times, tasks = [], 0
@@ -413,6 +439,150 @@ class BatchArm:
         return n
 
 
+class DNNInputs:
+    """The dynamic-DNN workload: inputs of a gated MLP with shared weights,
+    run one input per flush (the DAG of each input depends on its gates)."""
+
+    def __init__(self, torch, mode, window, cta_slots, seed=1, per_b=100):
+        import streamgen as sg
+        from paper_2401_12377_b300 import harness
+        self.torch = torch
+        shared = sg.dnn_weights(seed * 7919, 24)
+        self.shared = shared
+        self.streams = [sg.dnn_stream(seed * 100000 + b * 1000 + i, batch=b, blocks=24, weight_sets=24,
+                                      shared=shared, window=window)
+                        for b in (1, 2, 4, 8) for i in range(per_b)]
+        wdev = {"W": torch.from_numpy(shared[0]).cuda(), "B": torch.from_numpy(shared[1]).cuda()}
+        self.bufs, self.packed = [], []
+        for st in self.streams:
+            acts = {k: st.buffers[k] for k in ("h", "t", "u")}
+            b = harness.DeviceBuffers(acts)
+            b.t.update(wdev)
+            b.base.update({k: int(v.data_ptr()) for k, v in wdev.items()})
+            b.dtype.update({"W": np.dtype(np.float32), "B": np.dtype(np.float32)})
+            self.bufs.append(b)
+            self.packed.append(harness.pack_tasks(st.tasks, b))
+        self.pristine = [{k: b.t[k].clone() for k in ("h", "t", "u")} for b in self.bufs]
+        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots)
+        self.n_tasks = sum(len(st.tasks) for st in self.streams)
+
+    def reset_device(self):
+        for b, p in zip(self.bufs, self.pristine):
+            for k, v in p.items():
+                b.t[k].copy_(v, non_blocking=True)
+
+    def run_once(self, latencies=None):
+        n = 0
+        for ids, rows in self.packed:
+            t0 = time.perf_counter()
+            start = self.ctx.tail(0)
+            self.ctx.submit_packed(ids + np.uint32(start), rows)
+            self.ctx.flush()
+            self.ctx.sync()
+            if latencies is not None:
+                latencies.append(time.perf_counter() - t0)
+            n += len(ids)
+        return n
+
+
+def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+    W = args.window or 32
+    seed = 1 + rank
+    arm = DNNInputs(torch, "window", W, args.cta_slots, seed)
+    lat = []
+    if dist:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = time_arm(arm, args.steps, args.warmup, flush_buf, lat)
+    clocks = clk.summary()
+    ms_step = statistics.mean(res["ms"])
+    max_ms = max_over_ranks(ms_step, dist, "cuda")
+    tps = res["tasks"] / args.steps
+    st = res["stats"]
+    launches = st["launches"]
+    avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
+    bpl = st["device_seg_bytes"] / max(1, launches)
+    achieved = bpl / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    lus = np.sort(np.array(lat)) * 1e6
+    line = {"metric": METRIC, "value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DNN, "window": W, "inputs_per_step": len(arm.streams),
+                       "tasks_per_step": tps, "cta_slots": st.get("cta_slots"),
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "one GPU"},
+            "input_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bpl, "avg_launch_us": avg_launch_s * 1e6},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if not args.no_baselines:
+        for mode in ("inorder", "graph", "sw"):
+            b = DNNInputs(torch, mode, W, args.cta_slots, seed)
+            r = time_arm(b, max(1, min(args.steps, 3)), 1, flush_buf)
+            ms = statistics.mean(r["ms"])
+            k = max(1, min(args.steps, 3))
+            entry = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms,
+                     "kernel_ms_per_step": r["stats"]["kernel_ms"] / k}
+            if mode == "graph":
+                entry["host_build_instantiate_ms_per_step"] = (r["stats"]["graph_build_ms"]
+                                                               + r["stats"]["graph_instantiate_ms"]) / k
+                line["graph_with_build"] = entry
+                line["graph_launch"] = {"tasks_per_s": (r["tasks"] / k) / (entry["kernel_ms_per_step"] / 1e3),
+                                        "device_ms_per_step": entry["kernel_ms_per_step"]}
+                line["speedup_vs_graph_with_build"] = ms / ms_step
+                line["speedup_vs_graph_launch_only"] = entry["kernel_ms_per_step"] / ms_step
+            elif mode == "sw":
+                line["sw_host_scheduler"] = entry
+                line["speedup_vs_sw_host_scheduler"] = ms / ms_step
+            else:
+                line["inorder"] = entry
+                line["speedup_vs_inorder"] = ms / ms_step
+            b.ctx.close()
+    # end to end: each input's activations in from pinned memory, its output h back
+    pin_in = [{k: torch.from_numpy(st.buffers[k].view(np.uint8).copy()).pin_memory() for k in ("h", "t", "u")}
+              for st in arm.streams]
+    pin_out = [torch.empty(b.t["h"].numel(), dtype=torch.uint8).pin_memory() for b in arm.bufs]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    h2d = d2h = n = 0
+    for (ids, rows), b, pi, po in zip(arm.packed, arm.bufs, pin_in, pin_out):
+        for k, v in pi.items():
+            b.t[k].copy_(v, non_blocking=True)
+            h2d += v.numel()
+        start = arm.ctx.tail(0)
+        arm.ctx.submit_packed(ids + np.uint32(start), rows)
+        arm.ctx.flush()
+        arm.ctx.sync()
+        po.copy_(b.t["h"], non_blocking=True)
+        d2h += po.numel()
+        n += len(ids)
+    ev1.record()
+    torch.cuda.synchronize()
+    e_ms = ev0.elapsed_time(ev1)
+    line["e2e"] = {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": int(h2d + 320 * n), "d2h_bytes_per_step": int(d2h)}
+    arm.ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import execute
+        t0 = time.perf_counter()
+        n = k = 0
+        while k < len(arm.streams) and time.perf_counter() - t0 < 10.0:
+            st = arm.streams[k]
+            execute.run_inorder(st.buffers, st.tasks)
+            n += len(st.tasks)
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {k} inputs of the step ({n} tasks), single-threaded numpy, "
+                                          f"{dt:.1f} s"}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    return line
+
+
 def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     """64 independent streams of uneven length in one persistent launch, window
     and CTA slots from the autotuner; lockstep host-driven baselines."""
@@ -480,7 +650,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
 
     if not args.no_baselines:
         steps_b = max(1, min(args.steps, 3))
-        for mode, key in (("window", "window_host_driven"), ("inorder", "inorder"), ("graph", "graph")):
+        for mode, key in (("window", "window_host_driven"), ("inorder", "inorder"), ("graph", "graph"),
+                          ("sw", "sw_host_scheduler")):
             c2 = harness.Context(W, mode=mode, n_streams=S, cta_slots=slots, timing=True, capacity=cap)
             hd = harness.BatchedHostDriven(specs, c2)
             r = time_arm(BatchArm(torch, hd, c2), steps_b, 1, flush_buf)
@@ -500,6 +671,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                 key = "graph_with_build"
             elif mode == "inorder":
                 line["speedup_vs_inorder"] = ms / ms_step
+            elif mode == "sw":
+                line["speedup_vs_sw_host_scheduler"] = ms / ms_step
             line[key] = entry
             c2.close()
             del hd
@@ -639,9 +812,11 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream())
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     seed = 1 + rank
-    if args.workload in ("batched", "serving"):
+    if args.workload in ("dnn", "batched", "serving"):
         if args.workload == "batched":
             line = bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
+        elif args.workload == "dnn":
+            line = bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
         else:
             line = bench_serving(args, torch, dist, world, rank, peaks, peak_src)
         if rank == 0:
@@ -734,6 +909,15 @@ def main():
         line["speedup_kernel_time_vs_graph_launch"] = g_launch_ms / (kernel_ms / args.steps)
         inorder.ctx.close()
         graph.ctx.close()
+        swa = RLBench("sw", seed, args.window, args.cta_slots)
+        r_sw = time_arm(swa, max(1, min(args.steps, 3)), 1, flush_buf)
+        ms_sw = statistics.mean(r_sw["ms"])
+        line["sw_host_scheduler"] = {"tasks_per_s": (r_sw["tasks"] / max(1, min(args.steps, 3))) / (ms_sw / 1e3),
+                                     "ms_per_step": ms_sw, "threads": 8,
+                                     "note": "the paper's software scheduler: host window, 8 threads x one "
+                                             "CUDA stream, cudaStreamSynchronize per task"}
+        line["speedup_vs_sw_host_scheduler"] = ms_sw / ms_step
+        swa.ctx.close()
 
     # ---- end to end through the API with host buffers ---------------------------------------
     line["e2e"] = time_e2e(acs_arm, max(1, min(args.steps, 3)))

@@ -145,7 +145,15 @@ typedef struct { uint64_t y; uint64_t ns; float tag; uint32_t pad; } acs_sleep_a
 enum acs_mode {
     ACS_MODE_WINDOW = 0,   /* the method: persistent device scheduler (default) */
     ACS_MODE_INORDER = 1,  /* baseline: one kernel launch per task, one CUDA stream */
-    ACS_MODE_GRAPH = 2     /* baseline: per flush, a CUDA graph of the full DAG */
+    ACS_MODE_GRAPH = 2,    /* baseline: per flush, a CUDA graph of the full DAG */
+    ACS_MODE_SW = 3        /* baseline: the paper's software scheduler (Sec. IV-B, Alg. 2):
+                              a host-side window of W tasks per stream checked with the
+                              same overlap test, completed tasks leave the window out of
+                              order; sw_threads host threads each launch one ready task
+                              at a time into their own CUDA stream and wait for it with
+                              cudaStreamSynchronize. acs_flush returns when every
+                              flushed task completed; kernel_ms then holds the flushes'
+                              host wall time */
 };
 
 enum acs_flags {
@@ -176,7 +184,8 @@ typedef struct acs_config {
     uint32_t idle_limit_ms; /* resident launches (acs_start): the kernel leaves by
                                itself after this long idle without any host call
                                (0 -> 10 000 ms), so it always terminates */
-    uint32_t reserved[4];   /* must be 0 */
+    uint32_t sw_threads;    /* ACS_MODE_SW: host threads, one CUDA stream each (0 -> 8) */
+    uint32_t reserved[3];   /* must be 0 */
 } acs_config;
 
 typedef struct acs_stats {

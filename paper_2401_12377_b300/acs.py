@@ -36,7 +36,7 @@ OPS = {"nop": 0, "axpy": 1, "scale": 2, "add": 3, "gemv": 4, "bias_relu": 5, "re
        "rl_broadphase": 10, "rl_solve": 11, "rl_integrate": 12, "rl_emit": 13, "wait_flag": 30,
        "sleep": 31}
 
-ACS_MODE_WINDOW, ACS_MODE_INORDER, ACS_MODE_GRAPH = 0, 1, 2
+ACS_MODE_WINDOW, ACS_MODE_INORDER, ACS_MODE_GRAPH, ACS_MODE_SW = 0, 1, 2, 3
 ACS_FLAG_LOG, ACS_FLAG_TIMING, ACS_FLAG_TRACE = 1, 2, 4
 
 ACS_RL_SPHERES = 32
@@ -57,7 +57,7 @@ class acs_config(C.Structure):
                 ("capacity", C.c_uint32), ("log_capacity", C.c_uint32), ("flags", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("poll_ns", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("idle_limit_ms", C.c_uint32),
-                ("reserved", C.c_uint32 * 4)]
+                ("sw_threads", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class acs_stats(C.Structure):

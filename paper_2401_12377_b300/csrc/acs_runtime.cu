@@ -11,6 +11,9 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -54,6 +57,29 @@ uint32_t log2_pow2(uint32_t v) {
 
 }  // namespace
 
+// ACS_MODE_SW: the paper's software scheduler on the host (Sec. IV-B, Alg. 2).
+struct SwTask {
+    uint32_t stream, q;             // stream and position
+    uint32_t up = 0;                // upstream tasks not yet complete
+    std::vector<uint32_t> down;     // tasks waiting on this one
+};
+
+struct SwState {
+    std::mutex m;
+    std::condition_variable work;   // threads: a ready task or shutdown
+    std::condition_variable idle;   // flush: every task complete or an error
+    std::vector<std::thread> threads;
+    std::vector<cudaStream_t> streams;
+    bool shutdown = false;
+    std::vector<SwTask> tasks;                 // this flush's tasks, stream by stream
+    std::deque<uint32_t> ready;                // oldest first
+    std::vector<std::vector<uint32_t>> window; // per stream: tasks inserted and not complete
+    std::vector<uint32_t> next, end;           // per stream: next task to insert, one past the last
+    uint32_t remaining = 0;         // tasks of this flush not yet complete
+    uint32_t inflight = 0;          // tasks a thread launched and has not completed
+    int err = 0;
+};
+
 struct acs_ctx {
     acs_config cfg{};
     uint32_t W = 0, S = 0, C = 0, cap_log2 = 0, LC = 0, log_log2 = 0;
@@ -88,6 +114,8 @@ struct acs_ctx {
     cudaGraphExec_t last_exec = nullptr;
     std::vector<cudaGraphExec_t> execs_pending;
     std::vector<cudaGraph_t> graphs_pending;
+    // software scheduler (ACS_MODE_SW)
+    SwState *sw = nullptr;
 };
 
 namespace {
@@ -298,6 +326,131 @@ int flush_resident(acs_ctx *c) {
     return ACS_OK;
 }
 
+// ---- software scheduler (ACS_MODE_SW) ---------------------------------------------
+
+const TaskRec &sw_rec(acs_ctx *c, const SwTask &t) {
+    return c->h_ring[(size_t)t.stream * c->C + (t.q & (c->C - 1))];
+}
+
+// window module, insertion: the next tasks of stream s enter while the window
+// has room; each is checked against every task still in the window (caller
+// holds the lock)
+void sw_insert(acs_ctx *c, uint32_t s) {
+    SwState &w = *c->sw;
+    auto &win = w.window[s];
+    while (win.size() < c->W && w.next[s] < w.end[s]) {
+        const uint32_t j = w.next[s]++;
+        SwTask &tj = w.tasks[j];
+        const TaskRec &rj = sw_rec(c, tj);
+        for (uint32_t i : win)
+            if (recs_conflict(sw_rec(c, w.tasks[i]), rj)) {
+                w.tasks[i].down.push_back(j);
+                tj.up++;
+            }
+        win.push_back(j);
+        if (tj.up == 0) w.ready.push_back(j);
+    }
+}
+
+// scheduler module: one thread, one CUDA stream, one task in flight
+void sw_thread(acs_ctx *c, uint32_t k) {
+    SwState &w = *c->sw;
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(w.m);
+    while (true) {
+        w.work.wait(lk, [&] { return w.shutdown || (!w.ready.empty() && !w.err); });
+        if (w.shutdown) return;
+        const uint32_t j = w.ready.front();
+        w.ready.pop_front();
+        w.inflight++;
+        const TaskRec &r = sw_rec(c, w.tasks[j]);
+        lk.unlock();
+        TaskHdr h;
+        std::memcpy(&h, &r, sizeof h);
+        void *args[] = {&h};
+        cudaError_t e = cudaLaunchKernel(body_kernel_fn(), dim3(r.ncta), dim3(kBlock), args, kBodySmem, w.streams[k]);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(w.streams[k]);
+        lk.lock();
+        if (e != cudaSuccess && !w.err) w.err = e == cudaErrorMemoryAllocation ? ACS_ERR_NOMEM : ACS_ERR_DEVICE;
+        // window module, completion: release dependents, free the slot
+        SwTask &t = w.tasks[j];
+        for (uint32_t d : t.down)
+            if (--w.tasks[d].up == 0) w.ready.push_back(d);
+        auto &win = w.window[t.stream];
+        win.erase(std::find(win.begin(), win.end(), j));
+        sw_insert(c, t.stream);
+        c->stats.launches++;
+        w.inflight--;
+        if (--w.remaining == 0 || w.err || !w.inflight) w.idle.notify_all();
+        w.work.notify_all();
+    }
+}
+
+int sw_start(acs_ctx *c) {
+    c->sw = new (std::nothrow) SwState();
+    if (!c->sw) return ACS_ERR_NOMEM;
+    const uint32_t K = c->cfg.sw_threads ? c->cfg.sw_threads : 8u;
+    c->sw->streams.resize(K, nullptr);
+    for (auto &st : c->sw->streams)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return ACS_ERR_DEVICE;
+    for (uint32_t k = 0; k < K; ++k) c->sw->threads.emplace_back(sw_thread, c, k);
+    return ACS_OK;
+}
+
+void sw_stop(acs_ctx *c) {
+    if (!c->sw) return;
+    {
+        std::lock_guard<std::mutex> g(c->sw->m);
+        c->sw->shutdown = true;
+    }
+    c->sw->work.notify_all();
+    for (auto &t : c->sw->threads) t.join();
+    for (auto st : c->sw->streams)
+        if (st) cudaStreamDestroy(st);
+    delete c->sw;
+    c->sw = nullptr;
+}
+
+int flush_sw(acs_ctx *c) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    // the caller's earlier work on its stream (buffer copies) comes first
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    SwState &w = *c->sw;
+    std::unique_lock<std::mutex> lk(w.m);
+    w.tasks.clear();
+    w.ready.clear();
+    w.window.assign(c->S, {});
+    w.next.assign(c->S, 0);
+    w.end.assign(c->S, 0);
+    w.err = 0;
+    for (uint32_t s = 0; s < c->S; ++s) {
+        w.next[s] = (uint32_t)w.tasks.size();
+        for (uint32_t q = c->st[s].flushed; q != c->st[s].submitted; ++q) w.tasks.push_back(SwTask{s, q});
+        w.end[s] = (uint32_t)w.tasks.size();
+    }
+    w.remaining = (uint32_t)w.tasks.size();
+    for (uint32_t s = 0; s < c->S; ++s) sw_insert(c, s);
+    w.work.notify_all();
+    const auto limit = std::chrono::nanoseconds(c->cfg.timeout_ns);
+    uint32_t seen = w.remaining;
+    auto last = clk::now();
+    while (w.remaining && !w.err) {
+        w.idle.wait_for(lk, std::chrono::milliseconds(10));
+        if (w.remaining != seen) { seen = w.remaining; last = clk::now(); }
+        else if (clk::now() - last > limit) { w.err = ACS_ERR_TIMEOUT; break; }
+    }
+    const int err = w.err;
+    // threads launch nothing more after an error; wait for what they started
+    // (each of their waits is a cudaStreamSynchronize, which returns)
+    while (w.inflight) w.idle.wait_for(lk, std::chrono::milliseconds(1));
+    w.ready.clear();
+    lk.unlock();
+    c->stats.kernel_ms += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    return err ? fail(c, err) : ACS_OK;
+}
+
 int flush_inorder(acs_ctx *c) {
     const bool timing = (c->cfg.flags & ACS_FLAG_TIMING) != 0;
     TimedLaunch t{};
@@ -454,6 +607,7 @@ int acs_error(const acs_ctx *ctx) { return ctx ? ctx->err : ACS_ERR_INVALID; }
 void acs_destroy(acs_ctx *c) {
     if (!c) return;
     if (c->resident) acs_stop(c);
+    sw_stop(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     release_graphs(c, false);
     for (auto &t : c->timed) c->event_pool.push_back(t);
@@ -496,7 +650,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     }
     if (window < 1 || window > (uint32_t)kMaxWindow) return ACS_ERR_INVALID;
     if (cfg.n_streams > ACS_MAX_STREAMS) return ACS_ERR_INVALID;
-    if (cfg.mode > ACS_MODE_GRAPH) return ACS_ERR_INVALID;
+    if (cfg.mode > ACS_MODE_SW) return ACS_ERR_INVALID;
     if (cfg.capacity > (1u << 24)) return ACS_ERR_INVALID;
 
     acs_ctx *c = new (std::nothrow) acs_ctx();
@@ -591,6 +745,10 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     if (cfg.mode == ACS_MODE_WINDOW && max_grid <= c->S) { acs_destroy(c); return ACS_ERR_INVALID; }
     uint32_t slots = cfg.cta_slots ? cfg.cta_slots : (max_grid > c->S ? max_grid - c->S : 0);
     if (cfg.mode == ACS_MODE_WINDOW && (slots == 0 || slots + c->S > max_grid)) { acs_destroy(c); return ACS_ERR_INVALID; }
+    if (cfg.mode == ACS_MODE_SW) {
+        rc = sw_start(c);
+        if (rc) { acs_destroy(c); return rc; }
+    }
     c->cta_slots = slots;
     c->grid = slots + c->S;
     c->stats.cta_slots = c->cta_slots;
@@ -747,6 +905,7 @@ int acs_flush(acs_ctx *c) {
     if (c->resident) rc = flush_resident(c);
     else if (c->cfg.mode == ACS_MODE_WINDOW) rc = flush_window(c);
     else if (c->cfg.mode == ACS_MODE_INORDER) rc = flush_inorder(c);
+    else if (c->cfg.mode == ACS_MODE_SW) rc = flush_sw(c);
     else rc = flush_graph(c);
     if (rc) return rc;
     for (auto &s : c->st) {

@@ -120,7 +120,8 @@ def pack_tasks(tasks, bufs: DeviceBuffers):
     return ids, np.concatenate([pack_task(t, bufs) for t in tasks])
 
 
-MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph": acs.ACS_MODE_GRAPH}
+MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph": acs.ACS_MODE_GRAPH,
+         "sw": acs.ACS_MODE_SW}
 
 
 class Context:
@@ -129,7 +130,8 @@ class Context:
     def __init__(self, window: int, mode: str = "window", n_streams: int = 1, cta_slots: int = 0,
                  capacity: int = 0, log: bool = False, timing: bool = False, trace: bool = False,
                  timeout_s: float = 5.0, poll_ns: int = 0, ctas_per_sm: int = 0,
-                 cuda_stream: Optional[int] = None, resident: bool = False, idle_limit_ms: int = 0):
+                 cuda_stream: Optional[int] = None, resident: bool = False, idle_limit_ms: int = 0,
+                 sw_threads: int = 0):
         cfg = acs.acs_config_default()
         cfg.mode = MODES[mode]
         cfg.n_streams = n_streams
@@ -142,6 +144,7 @@ class Context:
         cfg.poll_ns = poll_ns
         cfg.ctas_per_sm = ctas_per_sm
         cfg.idle_limit_ms = idle_limit_ms
+        cfg.sw_threads = sw_threads
         # All device work of the context goes to one stream shared with torch, so
         # torch copies of the task buffers are ordered with the tasks. The legacy
         # default stream has no handle to share: then a torch stream is made

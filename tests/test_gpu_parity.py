@@ -113,6 +113,47 @@ def test_graph_mode_matches_in_order():
     assert_same(out_g, execute.run_inorder(s.buffers, s.tasks), "graph vs oracle")
 
 
+# ---- the paper's software scheduler (host window, K threads x one CUDA stream) ----------
+
+@pytest.mark.parametrize("seed", [0, 5, 9])
+@pytest.mark.parametrize("threads", [1, 4, 8])
+def test_sw_scheduler_matches_oracle(seed, threads):
+    s = sg.elementwise_stream(seed, n_tasks=120, ranges=True)
+    bufs = harness.DeviceBuffers(s.buffers)
+    with harness.Context(s.window, mode="sw", sw_threads=threads) as ctx:
+        ids, packed = harness.pack_tasks(s.tasks, bufs)
+        ctx.submit_packed(ids[:50], packed[:50])
+        ctx.flush()
+        ctx.submit_packed(ids[50:], packed[50:])
+        ctx.flush()
+        ctx.sync()
+        st = ctx.stats()
+    assert st["launches"] == len(s.tasks)
+    assert_same(bufs.download(), execute.run_inorder(s.buffers, s.tasks), "sw vs oracle")
+
+
+def test_sw_scheduler_dnn_and_streams():
+    streams = [sg.dnn_stream(40 + i, batch=1 + i, blocks=6) for i in range(3)]
+    bufs = [harness.DeviceBuffers(st.buffers) for st in streams]
+    with harness.Context(32, mode="sw", n_streams=3, sw_threads=6) as ctx:
+        for i, (st, b) in enumerate(zip(streams, bufs)):
+            ctx.submit(st.tasks, b, stream=i)
+        ctx.flush()
+        ctx.sync()
+    for st, b in zip(streams, bufs):
+        assert_close(b.download(), execute.run_inorder(st.buffers, st.tasks), DNN_RTOL)
+
+
+def test_sw_scheduler_rlsim_host_driven():
+    p = sg.RLParams(n_env=64, steps=4)
+    sim = sg.RLSim(4, p)
+    bufs = harness.DeviceBuffers(sim.buffers())
+    with harness.Context(32, mode="sw", sw_threads=8, capacity=1 << 14) as ctx:
+        harness.RLDriver(sim, bufs, ctx).run()
+    _, o_bufs, _ = execute.run_rlsim(sg.RLSim(4, p))
+    assert_same(bufs.download(), o_bufs, "sw rl vs oracle")
+
+
 def test_max_ncta_and_wide_tasks():
     s = sg.elementwise_stream(3, n_tasks=40, max_ncta=4)
     for t in s.tasks[::3]:
