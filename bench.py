@@ -71,6 +71,24 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
+# launch of the default workload, from the ncu capture summarised in
+# profiles/acs_persistent_kernel_rlsim_full.md; it applies only while the
+# kernel's sources hash to the value it was taken with (else traffic is null).
+KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
+                  "paper_2401_12377_b300/csrc/acs_internal.h")
+TRAFFIC_RLSIM = {"bytes_per_launch": 3770368, "sources_sha1": "7370f75abce4c988c3854be8efff0d4395603be1"}
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def ranks():
     """(world, rank, local rank) from the launcher's environment (1, 0, 0 alone)."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -859,7 +877,9 @@ def main():
             "run_latency_us": {"p50": lat_us[len(lat_us) // 2] if lat_us else None,
                                "p99": lat_us[min(len(lat_us) - 1, int(0.99 * len(lat_us)))] if lat_us else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_RLSIM["bytes_per_launch"]
+                         if kernel_sources_sha1() == TRAFFIC_RLSIM["sources_sha1"] else None,
                          "kernel": "acs_persistent_kernel", "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "avg_launch_us": avg_launch_s * 1e6,
