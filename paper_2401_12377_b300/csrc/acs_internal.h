@@ -30,12 +30,47 @@ struct alignas(16) TaskRec {
     uint16_t ncta;
     uint16_t wmask;      // bit k set: seg[k] is a write segment
     uint8_t nseg;
-    uint8_t flags;
+    uint8_t flags;       // bit k (k < 8): seg[k] is written and also read (see fold_reads)
     uint32_t seq;        // position of the task in its stream
     uint8_t args[48];
     Seg seg[kMaxSegs];
 };
 static_assert(sizeof(TaskRec) == 320, "TaskRec layout");
+
+// Drops every read segment that lies inside a write segment of the same task.
+// The dependency relation is unchanged: a write segment conflicts with every
+// segment of another task that a read segment inside it could conflict with
+// (read-after-write, write-after-read and write-after-write alike), so the
+// checks see fewer segment pairs and give the same masks. A read equal to a
+// write sets that write's bit in `flags`, so byte counts still see two
+// accesses (a read-modify-write range).
+__host__ __device__ inline void fold_reads(TaskRec &r) {
+    const uint32_t n = r.nseg < kMaxSegs ? r.nseg : kMaxSegs;
+    uint32_t drop = 0, rw = 0;
+    for (uint32_t x = 0; x < n; ++x) {
+        if ((r.wmask >> x) & 1u) continue;
+        for (uint32_t y = 0; y < n; ++y) {
+            if (!((r.wmask >> y) & 1u)) continue;
+            if (r.seg[x].start >= r.seg[y].start && r.seg[x].last <= r.seg[y].last) {
+                drop |= 1u << x;
+                if (r.seg[x].start == r.seg[y].start && r.seg[x].last == r.seg[y].last) rw |= 1u << y;
+                break;
+            }
+        }
+    }
+    if (!drop) return;
+    uint32_t out = 0, wm = 0, fl = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if ((drop >> k) & 1u) continue;
+        r.seg[out] = r.seg[k];
+        if ((r.wmask >> k) & 1u) wm |= 1u << out;
+        if (((rw >> k) & 1u) && out < 8) fl |= 1u << out;
+        ++out;
+    }
+    r.nseg = (uint8_t)out;
+    r.wmask = (uint16_t)wm;
+    r.flags = (uint8_t)fl;
+}
 
 // A descriptor in a scheduler's shared-memory history, padded to 336 bytes so
 // that 16-byte segment loads of consecutive records by the lanes of a warp hit
@@ -134,9 +169,12 @@ struct Mailbox {
     StreamProgress progress[ACS_MAX_STREAMS];
 };
 
-// Second word of a work-ring cell: the upstream slots the unit's worker must
-// still wait for (bit b: the task in window slot b) and the task's seq.
-struct alignas(16) CellAux {
+// What a worker needs beside its cell's payload, written once per task at
+// insertion and indexed like the descriptor ring: the upstream slots it must
+// still wait for (bit b: the task in window slot b) and the task's seq. Task
+// q + capacity reuses the entry only after task q retired, and every CTA of q
+// reads it before q can retire.
+struct alignas(16) TaskAux {
     unsigned long long up;
     uint32_t seq;
     uint32_t pad;
@@ -147,7 +185,7 @@ struct KParams {
     DevCtl *ctl;
     unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
                               // (descriptor index << 8 | CTA index)
-    CellAux *cellaux;         // [cells]
+    TaskAux *taskaux;         // [n_streams][capacity], like recs
     uint32_t *done;           // [n_streams][kMaxWindow]: seq + 1 of the slot's retired task
     uint32_t *remaining;      // [n_streams][kMaxWindow]: CTAs of the slot's task that finished
     unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
@@ -177,9 +215,24 @@ struct KParams {
 // predecessors of every task being checked plus look-ahead
 __host__ __device__ inline uint32_t hist_size(uint32_t window) { return window <= 32 ? 64u : 128u; }
 
+// Insertion batches handed from the scheduler warp to the publisher warp
+// (shared memory): per task its seq, work-ring offset, CTA count and upstream
+// mask still to wait for.
+constexpr uint32_t kPubSlots = 4;
+struct PubBatch {
+    unsigned long long up[32];
+    uint32_t q[32], off[32], n[32];
+    uint32_t nins, p0, total, pad;
+};
+struct PubQueue {
+    uint32_t produced, consumed, pad[2];
+    PubBatch b[kPubSlots];
+};
+
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    return H * 336u + H * 8 + H * 4 + 16 + 8 + kMaxWindow * 4;
+    const uint32_t base = H * 336u + H * 8 + H * 4 + 16 + 8 + kMaxWindow * 4;
+    return (base + 15u) / 16u * 16u + (uint32_t)sizeof(PubQueue);
 }
 
 inline uint32_t dyn_smem_bytes(uint32_t window) {

@@ -98,17 +98,18 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 //   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
 //   sh          counters shared by the warps
 //
-// Warps 1..5 ("checkers") compute the upstream-candidate mask of tasks
-// j = first + w + 5k: the segment-overlap test of Alg. 1 (extended to RAW) of
+// Warps 1..4 ("checkers") compute the upstream-candidate mask of tasks
+// j = first + w + 4k: the segment-overlap test of Alg. 1 (extended to RAW) of
 // task j against its W - 1 predecessors, one predecessor per lane, ballot ->
 // mask (bit i mod W for each conflicting i in [j - W + 1, j - 1]). The
 // candidate set of a task is fixed by the stream, so the test runs ahead of
-// execution, in parallel with it. Warp 6 polls the
-// done words of executing slots. Warp 7 loads descriptors. Warp 0 owns the
-// window: it inserts checked tasks into the W-slot ring, dispatching each at
-// once (its workers wait for the predecessors its mask names: the pending ->
-// ready transition happens at the worker), retires tasks the poller saw
-// complete and releases slots in program order.
+// execution, in parallel with it. Warp 5 publishes insertion batches to the
+// work ring. Warp 6 polls the done words of executing slots. Warp 7 loads
+// descriptors. Warp 0 owns the window: it inserts checked tasks into the
+// W-slot ring, dispatching each at once (its workers wait for the
+// predecessors its mask names: the pending -> ready transition happens at the
+// worker), retires tasks the poller saw complete and releases slots in
+// program order.
 
 struct SchedShared {
     uint32_t complete_upto;  // hist holds every seq below (loaded), from `lo`
@@ -124,6 +125,7 @@ struct SchedSmem {
     unsigned long long *pmask;
     uint32_t *ptag;
     SchedShared *sh;
+    PubQueue *pub;
     uint32_t H;
 };
 
@@ -142,6 +144,9 @@ __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     s.retired = reinterpret_cast<unsigned long long *>(p);
     p += sizeof(unsigned long long);
     s.expect = reinterpret_cast<uint32_t *>(p);
+    p += kMaxWindow * sizeof(uint32_t);
+    p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15u) & ~(uintptr_t)15u);
+    s.pub = reinterpret_cast<PubQueue *>(p);
     return s;
 }
 
@@ -153,7 +158,7 @@ __device__ __forceinline__ void sts_volatile(uint32_t *p, uint32_t v) { *(volati
 // The task being checked, its first kRegSegs segments held in registers
 // (the same for every lane; tasks with more segments read the rest from
 // shared memory).
-constexpr int kRegSegs = 6;
+constexpr int kRegSegs = 4;
 struct NewTask {
     Seg a[kRegSegs];
     uint32_t n, w;
@@ -348,7 +353,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     const bool open = P.open[stream] != 0 || P.resident != 0;
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
-    constexpr uint32_t kCheckers = kBlock / 32 - 3;   // warps 1 .. 5
+    constexpr uint32_t kCheckers = kBlock / 32 - 4;   // warps 1 .. 4
     unsigned long long tw = 0;
     unsigned long long seg_bytes = 0, check_cycles = 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
@@ -380,7 +385,9 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         if (lane == 0) {   // algorithmic bytes: what the task's segments name
             const TaskRec &rr = S.hist[j & HM].r;
             for (uint32_t k = 0; k < rr.nseg && k < (uint32_t)kMaxSegs; ++k)
-                if (!(rr.seg[k].start == 0 && rr.seg[k].last == ~0ull)) seg_bytes += rr.seg[k].last - rr.seg[k].start + 1;
+                if (!(rr.seg[k].start == 0 && rr.seg[k].last == ~0ull))
+                    seg_bytes += (rr.seg[k].last - rr.seg[k].start + 1) *
+                                 (1u + (k < 8 ? ((rr.wmask >> k) & (rr.flags >> k) & 1u) : 0u));
         }
         tw = 0;
         __threadfence_block();
@@ -430,6 +437,8 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     for (uint32_t i = threadIdx.x; i < (uint32_t)kMaxWindow; i += blockDim.x) S.expect[i] = 0;
     if (threadIdx.x == 0) {
         *S.retired = 0ull;
+        S.pub->produced = 0;
+        S.pub->consumed = 0;
         S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
         S.sh->next = first;
         S.sh->quit = 0;
@@ -444,10 +453,91 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     }
 }
 
+// Warp 5: publishes the scheduler's insertion batches, oldest first. Per
+// batch: each task's aux word (upstream still to wait for, seq), a check that
+// every work-ring cell it fills is free (its sequence word reads its
+// position), one fence.acq_rel.gpu, then the cells' sequence words. The fence
+// orders what the scheduler warp wrote or saw before handing the batch over
+// (log entries; retirements the poller acquired) before the new units.
+__device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t C = 1u << P.cap_log2;
+    SchedSmem S = carve(smem_raw, P.window);
+    const bool sole_producer = P.n_streams == 1;
+    uint32_t done_b = 0, backoff = 32;
+    uint32_t next_p0 = 0;                 // sole producer: where the next batch starts
+    unsigned long long pre0 = 0, pre1 = 0; // ... and its first 64 cells as last read
+    bool have_pre = false;
+    while (true) {
+        const uint32_t prod = lds_volatile(&S.pub->produced);
+        if (prod == done_b) {
+            if (lds_volatile(&S.sh->quit)) return;
+            __nanosleep(backoff);
+            if (backoff < 128) backoff <<= 1;
+            continue;
+        }
+        backoff = 32;
+        __threadfence_block();
+        const PubBatch &B = S.pub->b[done_b % kPubSlots];
+        const uint32_t nins = B.nins, p0 = B.p0, total = B.total;
+        const bool mine = lane < nins;
+        uint32_t q = 0, off = 0, n = 0, gidx = 0;
+        if (mine) {
+            q = B.q[lane];
+            off = B.off[lane];
+            n = B.n[lane];
+            gidx = (stream << P.cap_log2) | (q & (C - 1));
+            const unsigned long long up = B.up[lane];
+            *reinterpret_cast<uint4 *>(&P.taskaux[gidx]) = make_uint4((uint32_t)up, (uint32_t)(up >> 32), q, 0u);
+        }
+        // a cell is free for position p once its sequence word reads p
+        bool ok = true;
+        const bool pre_ok = sole_producer && have_pre && next_p0 == p0;
+        for (uint32_t u = lane; u < total && ok; u += 32) {
+            if (pre_ok && u < 64 && (uint32_t)(u < 32 ? pre0 : pre1) == p0 + u) continue;
+            unsigned long long *cell = &P.cells[(p0 + u) & P.cell_mask];
+            unsigned long long tw = 0;
+            uint32_t spins = 0;
+            while ((uint32_t)ld_relaxed_u64(cell) != p0 + u) {
+                if ((++spins & 63) == 0) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (tw == 0) tw = now;
+                    else if (now - tw > P.timeout_ns) {
+                        raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
+                        ok = false;
+                        break;
+                    }
+                    if (stopped(P)) { ok = false; break; }
+                }
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        fence_acq_rel_gpu();
+        __syncwarp();
+        if (mine) {
+            for (uint32_t c = 0; c < n; ++c) {
+                const uint32_t pos = p0 + off + c;
+                const uint32_t payload = (gidx << 8) | c;
+                st_relaxed_u64(&P.cells[pos & P.cell_mask],
+                               ((unsigned long long)payload << 32) | (unsigned long long)(pos + 1u));
+            }
+        }
+        ++done_b;
+        __syncwarp();
+        if (lane == 0) sts_volatile(&S.pub->consumed, done_b);
+        // look at the next 64 cells for the following batch (sole producer)
+        if (sole_producer) {
+            next_p0 = p0 + total;
+            pre0 = ld_relaxed_u64(&P.cells[(next_p0 + lane) & P.cell_mask]);
+            pre1 = ld_relaxed_u64(&P.cells[(next_p0 + 32 + lane) & P.cell_mask]);
+            have_pre = true;
+        }
+    }
+}
+
 __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
-    const uint32_t C = 1u << P.cap_log2;
     const uint32_t first = P.first[stream];
     const bool resident = P.resident != 0;
     const bool open = P.open[stream] != 0 || resident;
@@ -468,11 +558,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     uint32_t hslot = first % W, nslot = first % W;   // head % W, next % W
     const bool sole_producer = P.n_streams == 1;
     uint32_t tail = sole_producer ? ld_volatile_u32(&P.ctl->ring_tail) : 0u;
-    unsigned long long pre_cell0 = 0, pre_cell1 = 0;   // cells tail + lane, tail + 32 + lane
-    if (sole_producer) {
-        pre_cell0 = ld_relaxed_u64(&P.cells[(tail + lane) & P.cell_mask]);
-        pre_cell1 = ld_relaxed_u64(&P.cells[(tail + 32 + lane) & P.cell_mask]);
-    }
+    uint32_t pub_prod = 0;                          // batches handed to the publisher
     unsigned long long idle_since = 0;
     uint32_t iter = 0;
     bool failed = false;
@@ -509,7 +595,8 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
         // values of this iteration's insertion batch, published after retire
         bool mine = false;
-        uint32_t q = 0, my_n = 0, my_off = 0, js = 0, p0 = 0;
+        uint32_t q = 0, my_n = 0, my_off = 0, js = 0, p0 = 0, total = 0;
+        unsigned long long my_up = 0;
         // 2. insert and dispatch, lane k taking task next + k. Every task is
         //    dispatched when it enters the window: its worker CTAs wait for the
         //    checker's mask and then for the done words of the predecessors it
@@ -534,7 +621,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                 const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (uint32_t)o) incl += v;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            total = __shfl_sync(0xffffffffu, incl, 31);
             if (sole_producer) {
                 p0 = tail;
             } else {
@@ -544,42 +631,11 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
             tail = p0 + total;
             ACS_PHASE(3);
-            // a cell is free for position p once its sequence word reads p
-            // (the sole producer looked at the next 64 cells ahead of time)
-            bool ok = true;
-            for (uint32_t u = lane; u < total && ok; u += 32) {
-                if (sole_producer && u < 64 && (uint32_t)(u < 32 ? pre_cell0 : pre_cell1) == p0 + u) continue;
-                unsigned long long *cell = &P.cells[(p0 + u) & P.cell_mask];
-                unsigned long long tw = 0;
-                uint32_t spins = 0;
-                while ((uint32_t)ld_relaxed_u64(cell) != p0 + u) {
-                    if ((++spins & 63) == 0) {
-                        const unsigned long long now = globaltimer_ns();
-                        if (tw == 0) tw = now;
-                        else if (now - tw > P.timeout_ns) {
-                            raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
-                            ok = false;
-                            break;
-                        }
-                        if (stopped(P)) { ok = false; break; }
-                    }
-                }
-            }
-            if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
             ACS_PHASE(4);
-            // aux words (upstream still to wait for, seq) and log entries, then
-            // one release fence, then the sequence words that publish the units.
-            // The fence also orders the retirements seen through the poller
-            // (which acquired those done words) before the new tasks: conflicts
-            // farther back than W - 1 rely on that alone.
             js = nslot + lane >= W ? nslot + lane - W : nslot + lane;
             my_off = incl - my_n;
             if (mine) {
-                for (uint32_t c = 0; c < my_n; ++c) {
-                    CellAux *ax = &P.cellaux[(p0 + my_off + c) & P.cell_mask];
-                    ax->up = up;
-                    ax->seq = q;
-                }
+                my_up = up;
                 if (logging || tracing) {
                     const size_t li = lbase + (q & LM);
                     if (logging) {
@@ -642,22 +698,45 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             if (hslot >= W) hslot -= W;
         }
         ACS_PHASE(2);
-        // 5. publish this iteration's insertion batch (the aux stores above had
-        //    the retire step to complete before the fence)
+        // 5. hand this iteration's insertion batch to the publisher warp (its
+        //    fence then orders the log entries above and the retirements seen
+        //    through the poller before the new units: conflicts farther back
+        //    than W - 1 rely on that alone)
         if (nins) {
-            fence_acq_rel_gpu();
-            __syncwarp();
-            ACS_PHASE(6);
-            if (mine) {
-                S.expect[js] = q + 1u;             // the poller watches the slot from now on
-                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
-                for (uint32_t c = 0; c < my_n; ++c) {
-                    const uint32_t pos = p0 + my_off + c;
-                    const uint32_t payload = (gidx << 8) | c;
-                    st_relaxed_u64(&P.cells[pos & P.cell_mask],
-                                   ((unsigned long long)payload << 32) | (unsigned long long)(pos + 1u));
+            uint32_t spins = 0;
+            unsigned long long tw = 0;
+            bool ok = true;
+            while (pub_prod - lds_volatile(&S.pub->consumed) >= kPubSlots) {   // queue full: wait (bounded)
+                if ((++spins & 63) == 0) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (tw == 0) tw = now;
+                    else if (now - tw > P.timeout_ns) {
+                        if (lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
+                        ok = false;
+                        break;
+                    }
+                    if (stopped(P)) { ok = false; break; }
                 }
             }
+            if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+            PubBatch &B = S.pub->b[pub_prod % kPubSlots];
+            if (mine) {
+                B.up[lane] = my_up;
+                B.q[lane] = q;
+                B.off[lane] = my_off;
+                B.n[lane] = my_n;
+                S.expect[js] = q + 1u;             // the poller watches the slot from now on
+            }
+            if (lane == 0) {
+                B.nins = nins;
+                B.p0 = p0;
+                B.total = total;
+            }
+            __syncwarp();
+            __threadfence_block();
+            ++pub_prod;
+            if (lane == 0) sts_volatile(&S.pub->produced, pub_prod);
+            ACS_PHASE(6);
         }
         if (open && head != head_pub && lane == 0) {   // emitters wait on it for ring space
             st_relaxed_u32(&P.sctl[stream].head_pub, head);
@@ -711,11 +790,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         }
 
         ACS_PHASE(7);
-        // look at the next 64 cells for the following batch (sole producer)
-        if (sole_producer) {
-            pre_cell0 = ld_relaxed_u64(&P.cells[(tail + lane) & P.cell_mask]);
-            pre_cell1 = ld_relaxed_u64(&P.cells[(tail + 32 + lane) & P.cell_mask]);
-        }
 
         if (progress) {
             if (tracing) busy += clock64() - t0;
@@ -769,7 +843,8 @@ static_assert(sizeof(EmitSmem) <= kBodySmem, "emit smem");
 // One descriptor written straight into the stream's device ring: header, args
 // and the segments acs_get_addresses derives for the same args.
 __device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, uint16_t ncta, const void *args,
-                                        uint32_t args_bytes, const Seg *segs, uint32_t nseg, uint16_t wmask) {
+                                        uint32_t args_bytes, const Seg *segs, uint32_t nseg, uint16_t wmask,
+                                        uint8_t rw) {
     TaskHdr h;
     uint32_t *hw = reinterpret_cast<uint32_t *>(&h);
 #pragma unroll
@@ -779,6 +854,7 @@ __device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, u
     h.ncta = ncta;
     h.wmask = wmask;
     h.nseg = (uint8_t)nseg;
+    h.flags = rw;
     h.seq = seq;
     const uint32_t *aw = reinterpret_cast<const uint32_t *>(args);
     for (uint32_t i = 0; i < args_bytes / 4; ++i) hw[4 + i] = aw[i];
@@ -867,18 +943,20 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             const uint64_t e = E.env[k];
             acs_rl_solve_args x{cfg.pos + e * kPos, cfg.prop + e * kProp, cfg.cont + e * kRec, cfg.vel + e * kPos,
                                 cfg.beta_dt, cfg.slop};
+            // reads pos, prop, cont; reads and writes vel (one write segment: see fold_reads)
             sg[0] = seg_of(x.pos, kPos); sg[1] = seg_of(x.prop, kProp); sg[2] = seg_of(x.cont, kRec);
-            sg[3] = seg_of(x.vel, kPos); sg[4] = seg_of(x.vel, kPos);
+            sg[3] = seg_of(x.vel, kPos);
             const uint16_t nc = (uint16_t)min(max((uint32_t)E.nisl[k], 1u), 16u);
-            put_rec(r, seq, ACS_OP_RL_SOLVE, nc, &x, sizeof x, sg, 5, 1u << 4);
+            put_rec(r, seq, ACS_OP_RL_SOLVE, nc, &x, sizeof x, sg, 4, 1u << 3, 1u << 3);
         } else if (k < n_solve + n_chunks) {
             const uint64_t c = k - n_solve, e0 = c * chunk;
             acs_rl_integrate_args x{cfg.pos + e0 * kPos, cfg.vel + e0 * kPos, cfg.prop + e0 * kProp, chunk,
                                     cfg.dt, cfg.gdt, cfg.box};
-            sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.vel, chunk * kPos); sg[2] = seg_of(x.prop, chunk * kProp);
-            sg[3] = seg_of(x.pos, chunk * kPos); sg[4] = seg_of(x.vel, chunk * kPos);
+            // reads prop, reads and writes pos and vel (the host's folded order)
+            sg[0] = seg_of(x.prop, chunk * kProp);
+            sg[1] = seg_of(x.pos, chunk * kPos); sg[2] = seg_of(x.vel, chunk * kPos);
             const uint16_t nc = table[(a.step * 2 + 1) * n_chunks + c];
-            put_rec(r, seq, ACS_OP_RL_INTEGRATE, nc, &x, sizeof x, sg, 5, (1u << 3) | (1u << 4));
+            put_rec(r, seq, ACS_OP_RL_INTEGRATE, nc, &x, sizeof x, sg, 3, 6u, 6u);
         } else if (k < n_solve + 2 * n_chunks) {
             const uint64_t c = k - n_solve - n_chunks, e0 = c * chunk;
             acs_rl_broadphase_args x{cfg.pos + e0 * kPos, cfg.prop + e0 * kProp, cfg.cont + e0 * kRec,
@@ -886,7 +964,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.prop, chunk * kProp);
             sg[2] = seg_of(x.cont, chunk * kRec); sg[3] = seg_of(x.nisl, chunk * 4);
             const uint16_t nc = table[((a.step + 1) * 2 + 0) * n_chunks + c];
-            put_rec(r, seq, ACS_OP_RL_BROADPHASE, nc, &x, sizeof x, sg, 4, (1u << 2) | (1u << 3));
+            put_rec(r, seq, ACS_OP_RL_BROADPHASE, nc, &x, sizeof x, sg, 4, (1u << 2) | (1u << 3), 0u);
         } else {
             acs_rl_emit_args x = a;
             x.step = a.step + 1;
@@ -894,7 +972,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             sg[1] = seg_of(x.cfg, sizeof(acs_rl_emit_cfg));
             sg[2] = seg_of(x.ncta_table, (uint64_t)(x.steps + 1) * 2 * n_chunks);
             sg[3] = seg_of(x.token, 4);
-            put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3);
+            put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3, 0u);
         }
     }
     __syncthreads();
@@ -922,6 +1000,7 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
     const uint32_t ncells = P.cell_mask + 1u;
     const uint32_t W = P.window;
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nrec = P.n_streams << P.cap_log2;
     while (true) {
         if (threadIdx.x == 0) {
             // claim the next work-ring position and wait for its unit
@@ -947,7 +1026,16 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                 if (backoff < P.poll_ns) backoff <<= 1;
             }
             if (!quit) {
-                const uint4 ax = __ldcg(reinterpret_cast<const uint4 *>(&P.cellaux[pos & P.cell_mask]));
+                const uint32_t g = (uint32_t)(v >> 40);      // payload = gidx << 8 | cta
+                // the aux word and the task's header in one round trip
+                uint4 ax = make_uint4(0u, 0u, ~0u, 0u), h0 = ax, h1 = ax, h2 = ax, h3 = ax;
+                if (g < nrec) {
+                    const uint4 *hr = reinterpret_cast<const uint4 *>(P.recs + g);
+                    ax = __ldcg(reinterpret_cast<const uint4 *>(&P.taskaux[g]));
+                    h0 = __ldcg(hr); h1 = __ldcg(hr + 1); h2 = __ldcg(hr + 2); h3 = __ldcg(hr + 3);
+                }
+                uint4 *hd = reinterpret_cast<uint4 *>(&s_hdr);
+                hd[0] = h0; hd[1] = h1; hd[2] = h2; hd[3] = h3;
                 s_up = (unsigned long long)ax.x | ((unsigned long long)ax.y << 32);
                 s_seq = ax.z;
                 st_relaxed_u64(cell, (unsigned long long)(pos + ncells));  // free for the next lap
@@ -962,13 +1050,10 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         const uint32_t stream = gidx >> P.cap_log2;
         const uint32_t seq = s_seq;
         const uint32_t slot = seq % W;
-        const TaskRec *r = P.recs + gidx;
-        if (gidx >= (P.n_streams << P.cap_log2)) {   // self-check: payload names a ring entry
+        if (gidx >= nrec) {   // self-check: payload names a ring entry
             if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerPayload);
             continue;
         }
-        if (threadIdx.x < 4)
-            reinterpret_cast<uint4 *>(&s_hdr)[threadIdx.x] = __ldcg(reinterpret_cast<const uint4 *>(r) + threadIdx.x);
         // wait until every upstream task still active at dispatch retired: the
         // task in slot b is seq - ((seq - b) mod W); done words only grow
         const unsigned long long up = s_up;
@@ -1038,7 +1123,7 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
 
 // ---- kernels ----------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock, 3) acs_persistent_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(kBlock, 2) acs_persistent_kernel(const __grid_constant__ KParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (blockIdx.x < P.n_streams) {
         sched_init(P, blockIdx.x, smem);
@@ -1047,6 +1132,7 @@ __global__ void __launch_bounds__(kBlock, 3) acs_persistent_kernel(const __grid_
         if (warp == 0) scheduler_warp(P, blockIdx.x, smem);
         else if (warp == kBlock / 32 - 1) loader_warp(P, blockIdx.x, smem);
         else if (warp == kBlock / 32 - 2) poller_warp(P, blockIdx.x, smem);
+        else if (warp == kBlock / 32 - 3) publisher_warp(P, blockIdx.x, smem);
         else checker_warp(P, blockIdx.x, smem, warp - 1);
     } else {
         worker_loop(P, smem);

@@ -43,7 +43,7 @@ constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kOffRing = 0;
 constexpr size_t kOffCells = kOffRing + up(sizeof(TaskRec) * ACS_NOALLOC_MAX_TASKS);
 constexpr size_t kOffAux = kOffCells + up(sizeof(unsigned long long) * kNoAllocCells);
-constexpr size_t kOffCtl = kOffAux + up(sizeof(CellAux) * kNoAllocCells);
+constexpr size_t kOffCtl = kOffAux + up(sizeof(TaskAux) * ACS_NOALLOC_MAX_TASKS);
 constexpr size_t kOffDone = kOffCtl + up(sizeof(DevCtl));
 constexpr size_t kOffRemaining = kOffDone + up(sizeof(uint32_t) * kMaxWindow);
 constexpr size_t kOffLog = kOffRemaining + up(sizeof(uint32_t) * kMaxWindow);      // 3 x 1 entry
@@ -144,6 +144,7 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
         r.ncta = a.ncta;
         r.wmask = wmask;
         r.nseg = (uint8_t)cnt;
+        fold_reads(r);
         r.seq = i;
         std::memcpy(r.args, a.bytes, sizeof r.args);
     }
@@ -151,7 +152,7 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     unsigned char *base = d.scratch;
     TaskRec *ring = reinterpret_cast<TaskRec *>(base + kOffRing);
     unsigned long long *cells = reinterpret_cast<unsigned long long *>(base + kOffCells);
-    CellAux *aux = reinterpret_cast<CellAux *>(base + kOffAux);
+    TaskAux *aux = reinterpret_cast<TaskAux *>(base + kOffAux);
     DevCtl *ctl = reinterpret_cast<DevCtl *>(base + kOffCtl);
     uint32_t *done = reinterpret_cast<uint32_t *>(base + kOffDone);
     uint32_t *remaining = reinterpret_cast<uint32_t *>(base + kOffRemaining);
@@ -172,7 +173,7 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     P.recs = ring;
     P.ctl = ctl;
     P.cells = cells;
-    P.cellaux = aux;
+    P.taskaux = aux;
     P.done = done;
     P.remaining = remaining;
     P.log_mask = logs;

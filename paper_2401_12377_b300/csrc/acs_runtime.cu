@@ -91,7 +91,7 @@ struct acs_ctx {
     DevCtl *d_ctl = nullptr;
     uint32_t *d_done = nullptr, *d_remaining = nullptr;
     unsigned long long *d_cells = nullptr;
-    CellAux *d_cellaux = nullptr;
+    TaskAux *d_taskaux = nullptr;
     uint32_t ncells = 0;
     unsigned long long *d_log_mask = nullptr, *d_log_start = nullptr, *d_log_retire = nullptr;
     SchedStats *d_sched_stats = nullptr;
@@ -222,7 +222,7 @@ void fill_params(acs_ctx *c, KParams &P) {
     P.recs = c->d_ring;
     P.ctl = c->d_ctl;
     P.cells = c->d_cells;
-    P.cellaux = c->d_cellaux;
+    P.taskaux = c->d_taskaux;
     P.done = c->d_done;
     P.remaining = c->d_remaining;
     P.log_mask = c->d_log_mask;
@@ -620,7 +620,7 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_done);
     cudaFree(c->d_remaining);
     cudaFree(c->d_cells);
-    cudaFree(c->d_cellaux);
+    cudaFree(c->d_taskaux);
     cudaFree(c->d_log_mask);
     cudaFree(c->d_log_start);
     cudaFree(c->d_log_retire);
@@ -699,7 +699,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     while (cells < std::min<uint32_t>(2u * window * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
     c->ncells = std::max<uint32_t>(cells, 4096);
     chk(cudaMalloc(&c->d_cells, (size_t)c->ncells * sizeof(unsigned long long)));
-    chk(cudaMalloc(&c->d_cellaux, (size_t)c->ncells * sizeof(CellAux)));
+    chk(cudaMalloc(&c->d_taskaux, nrec * sizeof(TaskAux)));
     const bool keep_log = (cfg.flags & (ACS_FLAG_LOG | ACS_FLAG_TRACE)) != 0;
     if (!keep_log) c->log_log2 = 0, c->LC = 1;
     const size_t nlog = keep_log ? (size_t)c->S * c->LC : 1;
@@ -864,6 +864,7 @@ int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_a
     r.wmask = wmask;
     r.nseg = (uint8_t)cnt;
     r.flags = 0;
+    fold_reads(r);
     r.seq = ss.submitted;
     std::memcpy(r.args, args->bytes, sizeof r.args);
     ss.has_id = true;
