@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--window", type=int, default=0, help="window size (default: 32, or autotuned for batched)")
     ap.add_argument("--cta-slots", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
+    ap.add_argument("--window-study", action="store_true",
+                    help="rlsim: also time windows 8..64, ring and free-slot (span 64)")
     ap.add_argument("--no-baselines", action="store_true", help="skip the in-order / graph arms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     return ap.parse_args()
@@ -336,7 +338,7 @@ class ClockSampler:
 class RLBench:
     """One mode (window / inorder / graph) on one device state."""
 
-    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False):
+    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False, span=0):
         import torch
         import streamgen as sg
         from paper_2401_12377_b300 import harness
@@ -346,7 +348,8 @@ class RLBench:
         self.bufs = harness.DeviceBuffers(host)
         self.pristine = {k: v.clone() for k, v in self.bufs.t.items()}
         self.host_pinned = {k: torch.from_numpy(v.view("uint8").copy()).pin_memory() for k, v in host.items()}
-        self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots)
+        self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots,
+                                   span=span)
         self.emit = emit
         self.driver = (harness.RLEmitDriver if emit else harness.RLDriver)(self.sim, self.bufs, self.ctx)
         self.mode = mode
@@ -938,6 +941,21 @@ def main():
                                              "CUDA stream, cudaStreamSynchronize per task"}
         line["speedup_vs_sw_host_scheduler"] = ms_sw / ms_step
         swa.ctx.close()
+
+    # ---- window-size sensitivity: ring (span = window) and free-slot (span 64) ---------------
+    if args.window_study:
+        study = []
+        for span_mode in ("ring", "free-slot"):
+            for W in (8, 16, 32, 64):
+                if span_mode == "free-slot" and W == 64:
+                    continue
+                arm = RLBench("window", seed, W, args.cta_slots, emit=True, span=64 if span_mode == "free-slot" else 0)
+                r = time_arm(arm, max(1, min(args.steps, 3)), 1, flush_buf)
+                ms = statistics.mean(r["ms"])
+                study.append({"window": W, "span": 64 if span_mode == "free-slot" else W, "release": span_mode,
+                              "ms_per_run": ms, "tasks_per_s": (r["tasks"] / max(1, min(args.steps, 3))) / (ms / 1e3)})
+                arm.ctx.close()
+        line["window_study"] = study
 
     # ---- end to end through the API with host buffers ---------------------------------------
     line["e2e"] = time_e2e(acs_arm, max(1, min(args.steps, 3)))

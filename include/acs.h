@@ -185,7 +185,16 @@ typedef struct acs_config {
                                itself after this long idle without any host call
                                (0 -> 10 000 ms), so it always terminates */
     uint32_t sw_threads;    /* ACS_MODE_SW: host threads, one CUDA stream each (0 -> 8) */
-    uint32_t reserved[3];   /* must be 0 */
+    uint32_t span;          /* window mode: ring span M, window <= M <= 64 (0 -> M = window).
+                               M = window is the in-order ring: task j enters once every
+                               task <= j - W retired, and its candidates are tasks
+                               j - W + 1 .. j - 1. M > window is the free-slot variant
+                               (Sec. IV-B/IV-C): at most `window` tasks are inserted and
+                               not retired, a retired task frees its place at once (out
+                               of order), and candidates are the unretired tasks among
+                               j - M + 1 .. j - 1 (the M bound of the upstream load
+                               module); logs then give the masks over M - 1 predecessors */
+    uint32_t reserved[2];   /* must be 0 */
 } acs_config;
 
 typedef struct acs_stats {

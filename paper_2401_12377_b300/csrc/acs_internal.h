@@ -197,7 +197,8 @@ struct KParams {
     uint32_t cap_log2;        // capacity = 1 << cap_log2
     uint32_t log_log2;        // log_capacity = 1 << log_log2
     uint32_t cell_mask;       // work-ring cells - 1 (power of two)
-    uint32_t window;
+    uint32_t window;          // ring span M: slots, and the candidate distance M - 1
+    uint32_t active_limit;    // tasks inserted and not retired, at most (<= window)
     uint32_t n_streams;       // = scheduler CTAs (CTA s < n_streams schedules stream s)
     uint32_t flags;
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses

@@ -583,7 +583,16 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         //    mask reads (before the global polls below, so it never waits on them)
         uint32_t nins = 0;
         {
-            const uint32_t cap = min(min(end - next, W - (next - head)), 32u);
+            // room: ring positions (span W) and, with a smaller active limit,
+            // tasks not yet retired (retired ones free their place at once,
+            // out of order, while ring positions are released in order)
+            uint32_t room = min(W - (next - head), 32u);
+            if (P.active_limit < W) {
+                uint32_t act_n = __popc(__ballot_sync(0xffffffffu, st0 == kExec));
+                if (W > 32) act_n += __popc(__ballot_sync(0xffffffffu, st1 == kExec));
+                room = min(room, P.active_limit > act_n ? P.active_limit - act_n : 0u);
+            }
+            const uint32_t cap = min(end - next, room);
             const bool ok = lane < cap && lds_volatile(&S.ptag[(next + lane) & HM]) == next + lane + 1u;
             const uint32_t okm = __ballot_sync(0xffffffffu, ok);
             nins = __ffs(~okm) - 1;          // leading run of checked tasks

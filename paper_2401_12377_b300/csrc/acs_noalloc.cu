@@ -187,6 +187,7 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     P.log_log2 = 0;
     P.cell_mask = kNoAllocCells - 1;
     P.window = window;
+    P.active_limit = window;
     P.n_streams = 1;
     P.flags = 0;
     P.sched_smem = sched_smem_bytes(window);

@@ -83,6 +83,7 @@ struct SwState {
 struct acs_ctx {
     acs_config cfg{};
     uint32_t W = 0, S = 0, C = 0, cap_log2 = 0, LC = 0, log_log2 = 0;
+    uint32_t Wact = 0;   // active limit (the window); W is the ring span
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -237,6 +238,7 @@ void fill_params(acs_ctx *c, KParams &P) {
     P.log_log2 = c->log_log2;
     P.cell_mask = c->ncells - 1;
     P.window = c->W;
+    P.active_limit = c->Wact;
     P.n_streams = c->S;
     P.flags = c->cfg.flags;
     P.sched_smem = sched_smem_bytes(c->W);
@@ -338,7 +340,7 @@ const TaskRec &sw_rec(acs_ctx *c, const SwTask &t) {
 void sw_insert(acs_ctx *c, uint32_t s) {
     SwState &w = *c->sw;
     auto &win = w.window[s];
-    while (win.size() < c->W && w.next[s] < w.end[s]) {
+    while (win.size() < c->Wact && w.next[s] < w.end[s]) {
         const uint32_t j = w.next[s]++;
         SwTask &tj = w.tasks[j];
         const TaskRec &rj = sw_rec(c, tj);
@@ -649,6 +651,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
         if (!cfg.timeout_ns) cfg.timeout_ns = 5000000000ull;
     }
     if (window < 1 || window > (uint32_t)kMaxWindow) return ACS_ERR_INVALID;
+    if (cfg.span && (cfg.span < window || cfg.span > (uint32_t)kMaxWindow)) return ACS_ERR_INVALID;
     if (cfg.n_streams > ACS_MAX_STREAMS) return ACS_ERR_INVALID;
     if (cfg.mode > ACS_MODE_SW) return ACS_ERR_INVALID;
     if (cfg.capacity > (1u << 24)) return ACS_ERR_INVALID;
@@ -656,10 +659,11 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     acs_ctx *c = new (std::nothrow) acs_ctx();
     if (!c) return ACS_ERR_NOMEM;
     c->cfg = cfg;
-    c->W = window;
+    c->W = cfg.span ? cfg.span : window;
+    c->Wact = window;
     c->S = cfg.n_streams;
     uint32_t cap = std::max<uint32_t>(cfg.capacity, kMinCapacity);
-    cap = std::max<uint32_t>(cap, 2u * window + kPrefetch);
+    cap = std::max<uint32_t>(cap, 2u * c->W + kPrefetch);
     c->cap_log2 = log2_pow2(cap);
     c->C = 1u << c->cap_log2;
     if ((uint64_t)c->S * c->C > (1ull << 24)) {  // work-ring payload holds a 24-bit descriptor index
@@ -696,7 +700,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMalloc(&c->d_remaining, nslots * sizeof(uint32_t)));
     // work ring: at most (2W - 1) * ACS_MAX_NCTA units of one stream are in flight
     uint32_t cells = 1;
-    while (cells < std::min<uint32_t>(2u * window * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
+    while (cells < std::min<uint32_t>(2u * c->W * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
     c->ncells = std::max<uint32_t>(cells, 4096);
     chk(cudaMalloc(&c->d_cells, (size_t)c->ncells * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_taskaux, nrec * sizeof(TaskAux)));
@@ -725,7 +729,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(launch_init(c->d_cells, c->ncells, c->d_ctl, c->d_done, c->d_remaining, nslots, c->stream));
 
     // grid: one scheduler CTA per stream + worker CTAs, all co-resident
-    c->smem = dyn_smem_bytes(window);
+    c->smem = dyn_smem_bytes(c->W);
     if (cfg.ctas_per_sm) {
         // reserve enough shared memory that at most ctas_per_sm CTAs fit an SM
         int per_sm_smem = 0, per_block_optin = 0;

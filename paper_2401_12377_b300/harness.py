@@ -131,7 +131,7 @@ class Context:
                  capacity: int = 0, log: bool = False, timing: bool = False, trace: bool = False,
                  timeout_s: float = 5.0, poll_ns: int = 0, ctas_per_sm: int = 0,
                  cuda_stream: Optional[int] = None, resident: bool = False, idle_limit_ms: int = 0,
-                 sw_threads: int = 0):
+                 sw_threads: int = 0, span: int = 0):
         cfg = acs.acs_config_default()
         cfg.mode = MODES[mode]
         cfg.n_streams = n_streams
@@ -145,6 +145,7 @@ class Context:
         cfg.ctas_per_sm = ctas_per_sm
         cfg.idle_limit_ms = idle_limit_ms
         cfg.sw_threads = sw_threads
+        cfg.span = span
         # All device work of the context goes to one stream shared with torch, so
         # torch copies of the task buffers are ordered with the tasks. The legacy
         # default stream has no handle to share: then a torch stream is made
@@ -171,6 +172,7 @@ class Context:
             cuda_stream = cur.cuda_stream
         cfg.cuda_stream = C.c_void_p(cuda_stream)
         self.window, self.mode, self.n_streams = window, mode, n_streams
+        self.span = span or window   # ring span: logged masks are over span - 1 predecessors
         self.h = acs.acs_init(window, cfg)
         self.resident = False
         if resident:

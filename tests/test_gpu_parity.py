@@ -95,6 +95,45 @@ def test_cta_slot_counts_give_identical_outputs(slots):
     assert_same(out, execute.run_inorder(s.buffers, s.tasks), f"slots={slots}")
 
 
+# ---- the free-slot variant: W tasks in flight within a ring span M > W --------------------
+
+@pytest.mark.parametrize("W,M", [(1, 8), (4, 16), (8, 32), (16, 64), (32, 64)])
+def test_free_slot_variant(W, M):
+    """Logged candidates are the oracle's D_M (masks over M - 1 predecessors),
+    the ticket log is legal against E, outputs equal the oracle's, and no
+    task is inserted while W others are inserted and not retired."""
+    s = sg.elementwise_stream(13, n_tasks=200, ranges=True)
+    segs = addresses.stream_segments(s.tasks, s.buffers)
+    E = deps.full_dag(segs)
+    bufs = harness.DeviceBuffers(s.buffers)
+    with harness.Context(W, span=M, log=True, trace=True) as ctx:
+        ids, packed = harness.pack_tasks(s.tasks, bufs)
+        ctx.submit_packed(ids, packed)
+        ctx.flush()
+        ctx.sync()
+        masks, start, retire = ctx.log(0, 0, len(ids))
+        tr = ctx.trace(0, 0, len(ids)).astype(np.int64)
+    check_log(masks, start, retire, E, deps.window_dag(E, M), M)
+    assert_same(bufs.download(), execute.run_inorder(s.buffers, s.tasks), f"free slot W={W} M={M}")
+    ins, ret = tr[:, 0], tr[:, 4]
+    active = [int(np.sum(ret[:j] > ins[j])) for j in range(len(ids))]
+    assert max(active) <= W - 1
+
+
+def test_free_slot_rlsim_emission():
+    p = sg.RLParams(n_env=64, steps=5)
+    sim = sg.RLSim(6, p)
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    with harness.Context(16, span=64, log=True, capacity=1 << 12) as ctx:
+        n = harness.RLEmitDriver(sim, bufs, ctx).run()
+        masks, start, retire = ctx.log(0, 0, n)
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(6, p), emit=True)
+    assert n == len(o_tasks)
+    E = deps.full_dag(addresses.stream_segments(o_tasks, o_bufs))
+    check_log(masks, start, retire, E, deps.window_dag(E, 64), 64)
+    assert_same(bufs.download(), o_bufs, "free-slot rl vs oracle")
+
+
 @pytest.mark.parametrize("every", [1, 5, 16])
 def test_flush_splitting_keeps_the_window_dag(every):
     # windows continue across flushes: the logged DAG does not depend on how
