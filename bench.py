@@ -46,6 +46,8 @@ METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 l
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
 WORKLOAD_DNN = ("dynamic DNN: gated residual MLP, hidden 256, 24 blocks, shared weights; 100 inputs for each "
                 "batch size 1, 2, 4, 8, one flush (one launch) per input, window 32")
+WORKLOAD_STATIC = ("static irregular DAG: randomly wired network, 3 stages x 32 nodes (GEMV 256x256 of 1-8 CTAs, "
+                   "bias+ReLU, input aggregation), 411 tasks per input, 100 inputs per step, window 32")
 WORKLOAD_SERVING = ("serving: Poisson arrivals of rigid-sphere (64 envs, device-side emission) / gated-MLP "
                     "(batch 1-8, shared weights) requests of 100-5000 tasks, 20 GB budget, resident kernel")
 WORKLOAD_BATCHED = ("batched: 64 independent streams (alternating rigid-sphere 64 envs x 32 spheres / gated "
@@ -58,7 +60,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["acs", "reference"], default="acs")
-    ap.add_argument("--workload", choices=["rlsim", "dnn", "batched", "serving"], default="rlsim",
+    ap.add_argument("--workload", choices=["rlsim", "dnn", "static", "batched", "serving"], default="rlsim",
                     help="rlsim: one rigid-sphere stream (default); batched: 64 independent streams in one "
                          "launch; serving: Poisson arrivals over a resident kernel (steps = seconds of arrivals)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
@@ -196,6 +198,26 @@ def run_reference(args):
     import streamgen as sg
     from oracle import execute
     execute.build_c()
+    if args.workload == "static":
+        st = sg.random_wire_stream(1)
+        execute.run_inorder(st.buffers, st.tasks)
+        times = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            for i in range(10):                      # a bounded sample: 10 of the step's 100 inputs
+                execute.run_inorder(st.buffers, st.tasks)
+            times.append(time.perf_counter() - t0)
+        tasks = 10 * args.steps * len(st.tasks)
+        value = tasks / sum(times)
+        line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": 1, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD_STATIC, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                 "sample": "each step 10 of the 100 inputs, single-threaded"},
+                "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "dnn":
         shared = sg.dnn_weights(7919, 24)
         streams = [sg.dnn_stream(100000 + b * 1000 + i, batch=b, blocks=24, weight_sets=24, shared=shared)
@@ -604,6 +626,135 @@ def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     return line
 
 
+class StaticInputs:
+    """The static randomly wired network: one task graph, 100 inputs per
+    step. The window scheduler and the in-order / software baselines run
+    every input as its own flush; the CUDA graph is built for the first input
+    and replayed for every later one (inputs change only the data)."""
+
+    def __init__(self, torch, mode, window, cta_slots, seed=1, n_inputs=100):
+        import streamgen as sg
+        from paper_2401_12377_b300 import harness
+        self.torch, self.mode = torch, mode
+        self.stream = sg.random_wire_stream(seed, window=window)
+        self.bufs = harness.DeviceBuffers(self.stream.buffers)
+        rng = np.random.default_rng(seed + 17)
+        self.inputs = torch.from_numpy(rng.uniform(-1, 1, (n_inputs, 256)).astype(np.float32)).cuda()
+        self.ids, self.rows = harness.pack_tasks(self.stream.tasks, self.bufs)
+        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots)
+        self.x0 = self.bufs.t["x"][:1024].view(torch.float32)
+        self.built = False
+
+    def reset_device(self):
+        pass
+
+    def run_once(self, latencies=None):
+        n = 0
+        for i in range(self.inputs.shape[0]):
+            t0 = time.perf_counter()
+            self.x0.copy_(self.inputs[i], non_blocking=True)
+            if self.mode == "graph" and self.built:
+                self.ctx.replay()
+            else:
+                self.ctx.submit_packed(self.ids + np.uint32(self.ctx.tail(0)), self.rows)
+                self.ctx.flush()
+                self.built = True
+            self.ctx.sync()
+            if latencies is not None:
+                latencies.append(time.perf_counter() - t0)
+            n += len(self.ids)
+        return n
+
+
+def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+    W = args.window or 32
+    seed = 1 + rank
+    arm = StaticInputs(torch, "window", W, args.cta_slots, seed)
+    lat = []
+    if dist:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = time_arm(arm, args.steps, args.warmup, flush_buf, lat)
+    clocks = clk.summary()
+    ms_step = statistics.mean(res["ms"])
+    max_ms = max_over_ranks(ms_step, dist, "cuda")
+    tps = res["tasks"] / args.steps
+    st = res["stats"]
+    launches = st["launches"]
+    avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
+    bpl = st["device_seg_bytes"] / max(1, launches)
+    achieved = bpl / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    lus = np.sort(np.array(lat)) * 1e6
+    line = {"metric": METRIC, "value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_STATIC, "window": W, "inputs_per_step": arm.inputs.shape[0],
+                       "tasks_per_step": tps, "cta_slots": st.get("cta_slots"),
+                       "l2": "flushed between timed steps (512 MiB write); 24 MB of weights per input",
+                       "parallelism": f"replicas x{world}" if world > 1 else "one GPU"},
+            "input_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bpl, "avg_launch_us": avg_launch_s * 1e6},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if not args.no_baselines:
+        k = max(1, min(args.steps, 3))
+        for mode in ("inorder", "graph", "sw"):
+            b = StaticInputs(torch, mode, W, args.cta_slots, seed)
+            r = time_arm(b, k, 1, flush_buf)
+            ms = statistics.mean(r["ms"])
+            entry = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms,
+                     "kernel_ms_per_step": r["stats"]["kernel_ms"] / k}
+            if mode == "graph":
+                entry["note"] = "graph built once (first warm-up input), replayed for every input"
+                line["graph_replay"] = entry
+                line["speedup_vs_graph_replay"] = ms / ms_step
+                line["speedup_vs_graph_replay_device_only"] = entry["kernel_ms_per_step"] / (st["kernel_ms"] / args.steps)
+            elif mode == "sw":
+                line["sw_host_scheduler"] = entry
+                line["speedup_vs_sw_host_scheduler"] = ms / ms_step
+            else:
+                line["inorder"] = entry
+                line["speedup_vs_inorder"] = ms / ms_step
+            b.ctx.close()
+    # end to end: each input in from pinned memory, the stage output back
+    pin_in = arm.inputs.cpu().pin_memory()
+    pin_out = torch.empty(256, dtype=torch.float32).pin_memory()
+    xout = arm.bufs.t["x"].view(torch.float32)[-256:]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    n = 0
+    for i in range(pin_in.shape[0]):
+        arm.x0.copy_(pin_in[i], non_blocking=True)
+        arm.ctx.submit_packed(arm.ids + np.uint32(arm.ctx.tail(0)), arm.rows)
+        arm.ctx.flush()
+        arm.ctx.sync()
+        pin_out.copy_(xout, non_blocking=True)
+        n += len(arm.ids)
+    ev1.record()
+    torch.cuda.synchronize()
+    e_ms = ev0.elapsed_time(ev1)
+    line["e2e"] = {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": int(pin_in.numel() * 4 + 320 * n), "d2h_bytes_per_step": int(1024 * pin_in.shape[0])}
+    arm.ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import execute
+        t0 = time.perf_counter()
+        n = k = 0
+        while time.perf_counter() - t0 < 10.0 and k < 200:
+            execute.run_inorder(arm.stream.buffers, arm.stream.tasks)
+            n += len(arm.stream.tasks)
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{k} inputs ({n} tasks), single-threaded numpy, {dt:.1f} s"}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    return line
+
+
 def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     """64 independent streams of uneven length in one persistent launch, window
     and CTA slots from the autotuner; lockstep host-driven baselines."""
@@ -833,11 +984,13 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream())
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     seed = 1 + rank
-    if args.workload in ("dnn", "batched", "serving"):
+    if args.workload in ("dnn", "static", "batched", "serving"):
         if args.workload == "batched":
             line = bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
         elif args.workload == "dnn":
             line = bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
+        elif args.workload == "static":
+            line = bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
         else:
             line = bench_serving(args, torch, dist, world, rank, peaks, peak_src)
         if rank == 0:

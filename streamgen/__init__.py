@@ -192,6 +192,84 @@ def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
 
 
 # ----------------------------------------------------------------------------
+# Static irregular DAG (randomly wired network of small GEMVs)
+# ----------------------------------------------------------------------------
+
+def small_world_dag(rng, n: int, k: int = 4, p: float = 0.75):
+    """Edges (u, v), u < v, of a Watts-Strogatz small-world graph (ring
+    lattice, each node joined to its k nearest neighbours, each edge rewired
+    with probability p to a uniform random node) oriented from the lower to
+    the higher node index, which makes it acyclic."""
+    edges = set()
+    for u in range(n):
+        for d in range(1, k // 2 + 1):
+            v = (u + d) % n
+            if rng.random() < p:
+                w = int(rng.integers(0, n))
+                while w == u or (min(u, w), max(u, w)) in edges:
+                    w = int(rng.integers(0, n))
+                v = w
+            a, b = min(u, v), max(u, v)
+            if a != b:
+                edges.add((a, b))
+    return sorted(edges)
+
+
+def random_wire_stream(seed: int, n_nodes: int = 32, stages: int = 3, k: int = 4, p: float = 0.75,
+                       hidden: int = 256, window: int = 32, x: Optional[np.ndarray] = None) -> Stream:
+    """A static, randomly wired network (the shape of the paper's RandomWire
+    and NAS-cell workloads: an irregular DAG of many small kernels, batch 1).
+    Each stage is a small-world DAG of ``n_nodes`` nodes; node v aggregates
+    the outputs of its predecessors (or the stage input when it has none)
+    into h_v (one ``scale`` by 1 then one ``axpy`` by 1 per further input),
+    then y_v = relu(W_v h_v + b_v) (GEMV with 1..8 CTAs, then bias+ReLU). The
+    stage output, the next stage's input, sums the outputs of nodes without
+    successors. The task graph is the same for every input ``x``."""
+    rng = np.random.default_rng(seed)
+    H = hidden
+    N = n_nodes * stages
+    Wt = rng.uniform(-1.0 / 16, 1.0 / 16, (N, H, H)).astype(np.float32)
+    Bt = rng.uniform(-1.0 / 16, 1.0 / 16, (N, H)).astype(np.float32)
+    xs = np.zeros((stages + 1) * H, np.float32)
+    xs[:H] = rng.uniform(-1.0, 1.0, H).astype(np.float32)   # drawn always: the wiring below
+    if x is not None:                                         # must not depend on the input
+        xs[:H] = x
+    bufs = {"W": Wt.reshape(-1), "B": Bt.reshape(-1), "x": xs,
+            "h": np.zeros(N * H, np.float32), "y": np.zeros(N * H, np.float32)}
+    one = np.float32(1.0)
+    dims = {"m": np.uint32(H), "k": np.uint32(H)}
+    tasks: List[Task] = []
+
+    def add(op, ncta, arrays, scalars=None):
+        tasks.append(Task(len(tasks), op, ncta, arrays, dict(scalars or {})))
+
+    for st in range(stages):
+        edges = small_world_dag(rng, n_nodes, k, p)
+        preds = {v: [] for v in range(n_nodes)}
+        succ = {v: 0 for v in range(n_nodes)}
+        for u, v in edges:
+            preds[v].append(u)
+            succ[u] += 1
+        xin = Ref("x", st * H, H)
+        for v in range(n_nodes):
+            g = st * n_nodes + v
+            ins = [Ref("y", (st * n_nodes + u) * H, H) for u in preds[v]] or [xin]
+            hv = Ref("h", g * H, H)
+            add("scale", 1, {"x": ins[0], "y": hv}, {"a": one})
+            for r in ins[1:]:
+                add("axpy", 1, {"x": r, "y": hv}, {"a": one})
+            ncta = (1, 2, 4, 8)[mix(seed, 0x77, g) % 4]
+            add("gemv", ncta, {"W": Ref("W", g * H * H, H * H), "x": hv, "y": Ref("y", g * H, H)}, dims)
+            add("bias_relu", 1, {"t": Ref("y", g * H, H), "b": Ref("B", g * H, H)})
+        sinks = [v for v in range(n_nodes) if succ[v] == 0]
+        xout = Ref("x", (st + 1) * H, H)
+        add("scale", 1, {"x": Ref("y", (st * n_nodes + sinks[0]) * H, H), "y": xout}, {"a": one})
+        for v in sinks[1:]:
+            add("axpy", 1, {"x": Ref("y", (st * n_nodes + v) * H, H), "y": xout}, {"a": one})
+    return Stream(bufs, tasks, window, f"random_wire(seed={seed})")
+
+
+# ----------------------------------------------------------------------------
 # Rigid-body RL-simulation stream (E envs x S spheres; input-dependent DAG)
 # ----------------------------------------------------------------------------
 

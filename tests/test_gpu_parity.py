@@ -95,6 +95,38 @@ def test_cta_slot_counts_give_identical_outputs(slots):
     assert_same(out, execute.run_inorder(s.buffers, s.tasks), f"slots={slots}")
 
 
+# ---- static irregular DAG (randomly wired GEMV network) -------------------------------
+
+@pytest.mark.parametrize("seed,W", [(1, 32), (2, 8), (3, 64)])
+def test_random_wire_parity(seed, W):
+    s = sg.random_wire_stream(seed, n_nodes=16, stages=2, window=W)
+    E, D = oracle_dags(s)
+    out, st, (masks, start, retire) = harness.run_stream(s, log=True)
+    check_log(masks, start, retire, E, D, W)
+    ref_gpu, _, _ = harness.run_stream(s, mode="inorder")
+    assert_same(out, ref_gpu, "window vs in-order GPU")
+    assert_close(out, execute.run_inorder(s.buffers, s.tasks), DNN_RTOL)
+
+
+def test_random_wire_graph_replay_new_input():
+    """The graph of a static network is built once; replaying it after the
+    input changes gives the oracle's outputs for the new input."""
+    s = sg.random_wire_stream(4, n_nodes=16, stages=2)
+    bufs = harness.DeviceBuffers(s.buffers)
+    x2 = np.random.default_rng(9).uniform(-1, 1, 256).astype(np.float32)
+    with harness.Context(32, mode="graph") as ctx:
+        ctx.submit(s.tasks, bufs)
+        ctx.flush()
+        ctx.sync()
+        bufs.t["x"][:1024].copy_(torch.from_numpy(x2.view(np.uint8)))
+        ctx.replay()
+        ctx.sync()
+        st = ctx.stats()
+    assert st["launches"] == 2
+    s2 = sg.random_wire_stream(4, n_nodes=16, stages=2, x=x2)
+    assert_close(bufs.download(), execute.run_inorder(s2.buffers, s2.tasks), DNN_RTOL)
+
+
 # ---- the free-slot variant: W tasks in flight within a ring span M > W --------------------
 
 @pytest.mark.parametrize("W,M", [(1, 8), (4, 16), (8, 32), (16, 64), (32, 64)])

@@ -266,3 +266,22 @@ def test_serving_arrivals_and_catalogue():
     assert sum(c.kind == "rl" for c in cat) == 128
     assert all(100 <= c.target <= 5000 for c in cat)
     assert {c.dnn_batch for c in cat if c.kind == "dnn"} == {1, 2, 4, 8}
+
+
+def test_random_wire_inputs():
+    """The static randomly wired network: edges point from lower to higher
+    node index (acyclic), every node aggregates at least one input, the task
+    structure does not depend on the input vector, and the DAG's critical
+    path is far shorter than the stream (irregular parallelism)."""
+    rng = np.random.default_rng(3)
+    edges = sg.small_world_dag(rng, 32, 4, 0.75)
+    assert all(u < v for u, v in edges) and len(set(edges)) == len(edges)
+    assert 40 <= len(edges) <= 64
+    a = sg.random_wire_stream(1)
+    b = sg.random_wire_stream(1, x=np.ones(256, np.float32))
+    assert [(t.op, t.ncta, t.arrays) for t in a.tasks] == [(t.op, t.ncta, t.arrays) for t in b.tasks]
+    E = deps.full_dag(addresses.stream_segments(a.tasks, a.buffers))
+    depth = [1] * len(a.tasks)
+    for i, j in sorted(E, key=lambda e: e[1]):
+        depth[j] = max(depth[j], depth[i] + 1)
+    assert max(depth) * 3 < len(a.tasks)
