@@ -408,7 +408,8 @@ class RLBench:
 
 
 def l2_flush(buf):
-    buf.zero_()
+    if buf is not None:
+        buf.zero_()
 
 
 def time_arm(arm, steps, warmup, flush_buf, latencies=None):
@@ -416,7 +417,7 @@ def time_arm(arm, steps, warmup, flush_buf, latencies=None):
     for _ in range(warmup):
         arm.reset_device()
         arm.run_once()
-    torch.cuda.synchronize()
+    torch.cuda.current_stream().synchronize()
     st0 = arm.ctx.stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     tasks = 0
@@ -424,12 +425,12 @@ def time_arm(arm, steps, warmup, flush_buf, latencies=None):
     for k in range(steps):
         arm.reset_device()
         l2_flush(flush_buf)
-        torch.cuda.synchronize()
+        torch.cuda.current_stream().synchronize()
         w0 = time.perf_counter()
         ev[k][0].record()
         tasks += arm.run_once(latencies)
         ev[k][1].record()
-        torch.cuda.synchronize()
+        torch.cuda.current_stream().synchronize()
         wall += time.perf_counter() - w0
     ms = [a.elapsed_time(b) for a, b in ev]
     st1 = arm.ctx.stats()
@@ -781,19 +782,33 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                               capacity=cap)
         tuned["tune_s"] = time.perf_counter() - t0
         W, slots = tuned["window"], tuned["cta_slots"]
-    ctx = harness.Context(W, n_streams=S, cta_slots=slots, timing=True, capacity=cap)
+    # the kernel alone: one flush and one launch per pass (roofline from its launches)
+    ctx1 = harness.Context(W, n_streams=S, cta_slots=slots, timing=True, capacity=cap)
+    wl.bind(ctx1)
+    res1 = time_arm(BatchArm(torch, wl, ctx1), max(1, min(args.steps, 3)), 1, flush_buf)
+    ctx1.close()
+    # the method: a resident kernel, each stream published as soon as it is
+    # submitted (longest first); a pass ends when every stream is idle. CUDA
+    # events on this stream bracket each pass (the pass is host-synchronous).
+    # (pinned copies for the resets first: the resident kernel holds every SM,
+    # so resets go host to device, and there is no L2-flush kernel: the
+    # inputs, 384 MB of gated-MLP weights, are larger than L2)
+    wl.host_written()
+    wl.host_inputs()
+    wl.result_buffers()
+    ctx = harness.Context(W, n_streams=S, cta_slots=slots, timing=True, capacity=cap, resident=True)
     wl.bind(ctx)
     arm = BatchArm(torch, wl, ctx)
     latencies = []
     if dist:
         dist.barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        res = time_arm(arm, args.steps, args.warmup, flush_buf, latencies)
+        res = time_arm(arm, args.steps, args.warmup, None, latencies)
     clocks = clk.summary()
     ms_step = statistics.mean(res["ms"])
     tasks_per_step = res["tasks"] / args.steps
     max_ms = max_over_ranks(ms_step, dist, "cuda")
-    st = res["stats"]
+    st = res1["stats"]
     launches = st["launches"]
     avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
     bytes_per_launch = st["device_seg_bytes"] / max(1, launches)
@@ -806,8 +821,9 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             "config": {"workload": WORKLOAD_BATCHED, "streams": S, "window": W, "tasks_per_step": tasks_per_step,
                        "cta_slots": st.get("cta_slots"), "grid": st.get("grid"),
                        "stream_lengths": [sp.target for sp in specs],
-                       "mode": "window scheduler, one flush and one persistent launch for all streams",
-                       "l2": "flushed between timed steps (512 MiB write)",
+                       "mode": "window scheduler, one resident persistent launch for all streams; each "
+                               "stream published as soon as it is submitted",
+                       "l2": "not flushed between passes: inputs larger than L2 (384 MB of gated-MLP weights)",
                        "parallelism": f"independent batches x{world}" if world > 1 else "one GPU"},
             "autotune": None if tuned is None else {
                 "window": W, "cta_slots": slots, "tune_s": tuned.get("tune_s"), "cached": tuned.get("cached", False),
@@ -815,11 +831,35 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "acs_persistent_kernel",
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launches_from": "single-flush arm (one launch per pass, CUDA events around it)",
                          "avg_launch_us": avg_launch_s * 1e6,
                          "note": "bytes named by the tasks' read+write segments per launch / mean launch time"},
             "sched_cycles_per_task": st["sched_cycles"] / max(1, st["sched_inserts"]),
-            "gpu_launches": int(launches), "clocks": clocks}
+            "gpu_launches": 1, "gpu_launches_note": "one resident persistent launch runs through the timed region",
+            "single_flush": {"ms_per_step": statistics.mean(res1["ms"]),
+                             "tasks_per_s": (res1["tasks"] / max(1, min(args.steps, 3))) / (statistics.mean(res1["ms"]) / 1e3),
+                             "kernel_ms_per_step": avg_launch_s * 1e3,
+                             "note": "all streams submitted, then one flush and one launch per pass"},
+            "clocks": clocks}
 
+    # end to end: every stream's buffers in from pinned host memory, results out
+    reps = max(1, min(args.steps, 3))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # (the pinned buffers exist already: pinning while the kernel runs is slow)
+    torch.cuda.current_stream().synchronize()
+    tasks = h2d = d2h = 0
+    ev0.record()
+    for _ in range(reps):
+        h2d += wl.upload_host()
+        tasks += wl.run()
+        d2h += wl.download_results()
+    ev1.record()
+    torch.cuda.current_stream().synchronize()
+    e_ms = ev0.elapsed_time(ev1) / reps
+    desc = 320 * (tasks // reps)
+    line["e2e"] = {"value": (tasks / reps) / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": int(h2d // reps + desc), "d2h_bytes_per_step": int(d2h // reps)}
+    ctx.close()
     if not args.no_baselines:
         steps_b = max(1, min(args.steps, 3))
         for mode, key in (("window", "window_host_driven"), ("inorder", "inorder"), ("graph", "graph"),
@@ -849,25 +889,6 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             c2.close()
             del hd
 
-    # end to end: every stream's buffers in from pinned host memory, results out
-    reps = max(1, min(args.steps, 3))
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    wl.host_inputs()
-    wl.result_buffers()
-    torch.cuda.synchronize()
-    tasks = h2d = d2h = 0
-    ev0.record()
-    for _ in range(reps):
-        h2d += wl.upload_host()
-        tasks += wl.run()
-        d2h += wl.download_results()
-    ev1.record()
-    torch.cuda.synchronize()
-    e_ms = ev0.elapsed_time(ev1) / reps
-    desc = 320 * (tasks // reps)
-    line["e2e"] = {"value": (tasks / reps) / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
-                   "h2d_bytes_per_step": int(h2d // reps + desc), "d2h_bytes_per_step": int(d2h // reps)}
-    ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         execute_tasks, n_streams, dt = oracle_batch(seed, limit_s=10.0)
         line["cpu_baseline"] = {"value": execute_tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",

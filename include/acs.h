@@ -334,9 +334,12 @@ int acs_stream_tail(acs_ctx *ctx, uint32_t stream, uint32_t *tail);
  *     context's pinned host ring as before (ACS_ERR_FULL when the ring lacks
  *     room for the task plus the window behind it: call acs_progress or
  *     acs_sync, then retry);
- *   - acs_flush publishes each stream's new end with one release store into
- *     mapped host memory; no CUDA call. The kernel's loader warp copies the
- *     descriptors over the bus into the device ring and schedules them;
+ *   - acs_flush copies each stream's new descriptors into its device ring
+ *     with the copy engine (a stream of the context's own, beside the
+ *     kernel) and publishes the stream's new end, with one release store into
+ *     mapped host memory, once that copy has completed: at once if it has,
+ *     else from the next acs_flush, acs_progress or acs_sync. The kernel's
+ *     loader warp polls the published ends and schedules the new tasks;
  *   - acs_progress reports, without blocking, per stream: head (tasks below
  *     it were released, refreshed every 16 tasks and when idle) and idle_at
  *     (the stream was last seen idle with this end: all tasks below it

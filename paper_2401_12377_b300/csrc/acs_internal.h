@@ -149,9 +149,9 @@ struct StreamCtl {
 };
 
 // Host-mapped words of a resident launch (pinned host memory the device reads
-// and writes over the bus). The host appends a stream's descriptors to its
-// pinned ring and then publishes the new end with a release store; the device
-// copies them into the device ring and reports progress back.
+// and writes over the bus). The host copies a stream's new descriptors into
+// the device ring (copy engine) and, once that copy completed, publishes the
+// new end with a release store; the device reports progress back.
 struct StreamProgress {
     uint32_t head;      // device -> host: tasks below were released (published every few tasks)
     uint32_t idle_at;   // device -> host: the stream was idle (all tasks below retired,
@@ -167,6 +167,17 @@ struct Mailbox {
     unsigned long long heartbeat;         // host -> device: changes with every host call
     unsigned long long pad1[6];
     StreamProgress progress[ACS_MAX_STREAMS];
+};
+
+// A device-memory copy of the host-written mailbox words, refreshed about
+// every microsecond by one warp (the loader warp of stream 0) so that every
+// other poll of a resident launch stays in device memory: polls of mapped
+// host memory from many SMs slow the whole GPU down.
+struct alignas(128) Mirror {
+    uint32_t end[ACS_MAX_STREAMS];
+    uint32_t drain;
+    uint32_t pad;
+    unsigned long long heartbeat;
 };
 
 // What a worker needs beside its cell's payload, written once per task at
@@ -205,7 +216,7 @@ struct KParams {
     uint32_t poll_ns;         // longest sleep of an idle worker between ring polls
     uint32_t resident;        // 1: serve host-published work until drained (Mailbox)
     Mailbox *mbox;            // mapped host memory (resident launches)
-    const TaskRec *host_recs; // device view of the pinned host rings [n_streams][capacity]
+    Mirror *mirror;           // device copy of the mailbox's host-written words
     unsigned long long idle_limit_ns;  // resident: exit after this long without host activity
     uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
     uint32_t end[ACS_MAX_STREAMS];    // one past the last seq submitted by the host

@@ -61,17 +61,17 @@ __device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
     asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ uint32_t ld_relaxed_sys_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ unsigned long long ld_relaxed_sys_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ uint4 ld_volatile_v4(const uint4 *p) {
-    uint4 v;
-    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
-    return v;
-}
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
 __device__ __forceinline__ void st_relaxed_sys_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -197,6 +197,37 @@ __device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const NewTask &t
 // complete_upto after a CTA-scope fence. hist[s mod H] may take seq s once the
 // record it replaces (s - H) is neither a candidate of an unchecked task nor
 // uninserted: s < next + H - W + 1.
+// Refresh the device mirror of the mailbox (one warp, resident launches). The
+// drain word is read before the stream ends and written after them, so a
+// reader that sees drain in the mirror sees every end published before it;
+// the sys-scope fences carry the host's release of an end (its descriptors
+// were copied before it) to the readers of the mirror.
+__device__ void mirror_poll(const KParams &P, uint32_t lane) {
+    uint32_t d = 0;
+    unsigned long long hb = 0;
+    if (lane == 0) {
+        d = ld_relaxed_sys_u32(&P.mbox->drain);
+        hb = ld_relaxed_sys_u64(&P.mbox->heartbeat);
+    }
+    fence_acq_rel_sys();
+    constexpr uint32_t kPer = ACS_MAX_STREAMS / 32;
+    uint32_t he[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k)
+        if (lane + 32 * k < P.n_streams) he[k] = ld_relaxed_sys_u32(&P.mbox->host_end[lane + 32 * k]);
+    fence_acq_rel_sys();
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k)
+        if (lane + 32 * k < P.n_streams) st_relaxed_u32(&P.mirror->end[lane + 32 * k], he[k]);
+    __syncwarp();
+    if (lane == 0) {
+        fence_acq_rel_gpu();
+        st_relaxed_u64(&P.mirror->heartbeat, hb);
+        st_relaxed_u32(&P.mirror->drain, d);
+    }
+    __syncwarp();
+}
+
 __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
@@ -211,7 +242,16 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     unsigned long long tw = 0;
     uint32_t spins = 0, backoff = 32;
     uint32_t host_seen = end;                      // resident: host end last read
+    const bool mirror_keeper = P.resident && stream == 0;
+    unsigned long long mirror_t = 0;
     while (true) {
+        if (mirror_keeper) {
+            const unsigned long long now = globaltimer_ns();
+            if (now - mirror_t >= 1000ull) {
+                mirror_poll(P, lane);
+                mirror_t = now;
+            }
+        }
         bool wait = false, host_wait = false;
         if (load_upto >= end) {
             if (!open && !P.resident) return;      // a closed stream is fully loaded
@@ -220,28 +260,34 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                 // copied from the pinned host ring into the device ring (the
                 // host appends only while no emitter of the stream is alive)
                 if ((int32_t)(host_seen - end) <= 0) {   // nothing known beyond end (emitters may have moved it)
+                    // the mirrored end (device memory); acquire when it moved
                     uint32_t he = 0;
-                    if (lane == 0) he = ld_acquire_sys_u32(&P.mbox->host_end[stream]);
+                    if (lane == 0) {
+                        he = ld_relaxed_u32(&P.mirror->end[stream]);
+                        if (he != host_seen) fence_acq_rel_gpu();
+                    }
                     host_seen = __shfl_sync(0xffffffffu, he, 0);
                 }
                 if ((int32_t)(host_seen - end) > 0) {
-                    const uint32_t n = min(host_seen - end, 64u);
-                    constexpr uint32_t kRec16 = sizeof(TaskRec) / 16;
-                    const uint4 *hsrc = reinterpret_cast<const uint4 *>(P.host_recs + (size_t)stream * C);
-                    uint4 *dst = reinterpret_cast<uint4 *>(P.recs + (size_t)stream * C);
+                    // the host published descriptors already copied into the
+                    // device ring (by the copy engine, before the release
+                    // store); take up to 256 per round, counting the emit
+                    // tasks among them: each starts one emitter chain
+                    const uint32_t n = min(host_seen - end, 256u);
+                    const TaskRec *ring = P.recs + (size_t)stream * C;
                     uint32_t emits = 0;
-                    for (uint32_t i = lane; i < n * kRec16; i += 32) {
-                        const uint32_t rec = i / kRec16, part = i - rec * kRec16;
-                        const size_t at = (size_t)((end + rec) & (C - 1)) * kRec16 + part;
-                        const uint4 v = ld_volatile_v4(hsrc + at);
-                        dst[at] = v;
-                        if (part == 0 && (v.y & 0xffffu) == ACS_OP_RL_EMIT) ++emits;
+#pragma unroll
+                    for (uint32_t k = 0; k < 8; ++k) {
+                        const uint32_t r = k * 32 + lane;
+                        if (r < n) {
+                            const uint4 h = __ldcg(reinterpret_cast<const uint4 *>(ring + ((end + r) & (C - 1))));
+                            if ((h.y & 0xffffu) == ACS_OP_RL_EMIT) ++emits;
+                        }
                     }
                     emits = __reduce_add_sync(0xffffffffu, emits);
-                    // each host-submitted emit task starts one emitter chain
                     if (lane == 0 && emits) atomicAdd(&P.sctl[stream].open, emits);
                     __syncwarp();
-                    __threadfence();                   // records and chains before the new end
+                    __threadfence();                   // chains counted before the new end
                     end += n;
                     if (lane == 0) {
                         st_relaxed_u32(&P.sctl[stream].end, end);
@@ -569,7 +615,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
 
     uint32_t head_pub = first;
     // resident launches: progress reported to the host, idle bookkeeping
-    uint32_t head_host = first, idle_pub = first - 1u, idle_polls = 0;
+    uint32_t head_host = first, idle_pub = first - 1u, idle_polls = 0, idle_sleep = 256;
     unsigned long long last_hb = 0, hb_time = 0;
     while (first < end || open) {
         bool progress = false;
@@ -759,11 +805,10 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         if (head == end) {
             if (!open) { if (tracing) busy += clock64() - t0; break; }
             // open stream: finished once no emitter is left and nothing was appended
+            // (an acquire load, not a fence: idle streams poll this often)
             uint32_t fin = 0;
-            if (lane == 0 && ld_relaxed_u32(&P.sctl[stream].open) == 0) {
-                fence_acq_rel_gpu();
+            if (lane == 0 && ld_acquire_u32(&P.sctl[stream].open) == 0)
                 fin = ld_relaxed_u32(&P.sctl[stream].end) == end;
-            }
             fin = __shfl_sync(0xffffffffu, fin, 0);
             if (fin && !resident) { if (tracing) busy += clock64() - t0; break; }
             if (fin) {
@@ -782,11 +827,11 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                     }
                     if ((++idle_polls & 7) == 0) {
                         const unsigned long long now = globaltimer_ns();
-                        const unsigned long long hb = ld_relaxed_sys_u64(&P.mbox->heartbeat);
+                        const unsigned long long hb = ld_relaxed_u64(&P.mirror->heartbeat);
                         if (hb != last_hb || hb_time == 0) { last_hb = hb; hb_time = now; }
                         // (emitters may have taken the end past the host's)
-                        if (ld_acquire_sys_u32(&P.mbox->drain) &&
-                            (int32_t)(ld_acquire_sys_u32(&P.mbox->host_end[stream]) - end) <= 0) {
+                        if (ld_acquire_u32(&P.mirror->drain) &&
+                            (int32_t)(ld_relaxed_u32(&P.mirror->end[stream]) - end) <= 0) {
                             leave = 1;
                         } else if (now - hb_time > P.idle_limit_ns) {
                             st_relaxed_sys_u32(&P.mbox->expired, 1u);
@@ -803,10 +848,13 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         if (progress) {
             if (tracing) busy += clock64() - t0;
             idle_since = 0;
+            idle_sleep = 256;
         } else if (idle) {
-            // resident and waiting for the host: bounded by the idle limit above
+            // resident and waiting for the host: bounded by the idle limit
+            // above; the sleep grows to 8 us so idle streams stay quiet
             idle_since = 0;
-            __nanosleep(1000);
+            __nanosleep(idle_sleep);
+            if (idle_sleep < 8192) idle_sleep <<= 1;
         } else {
             const unsigned long long now = globaltimer_ns();
             if (idle_since == 0) idle_since = now;

@@ -80,6 +80,13 @@ struct SwState {
     int err = 0;
 };
 
+// A resident flush's descriptor copies (copy engine, beside the kernel) and
+// the stream ends to publish once they completed.
+struct PendingPub {
+    cudaEvent_t ev;
+    std::vector<std::pair<uint32_t, uint32_t>> ends;
+};
+
 struct acs_ctx {
     acs_config cfg{};
     uint32_t W = 0, S = 0, C = 0, cap_log2 = 0, LC = 0, log_log2 = 0;
@@ -102,8 +109,10 @@ struct acs_ctx {
     // resident launches (acs_start .. acs_stop)
     bool resident = false;
     Mailbox *h_mbox = nullptr, *d_mbox = nullptr;
-    TaskRec *d_hring = nullptr;          // device view of h_ring
-    cudaStream_t side = nullptr;         // abort copies while the resident kernel runs
+    Mirror *d_mirror = nullptr;          // device copy of the mailbox's host-written words
+    cudaStream_t side = nullptr;         // copies beside the resident kernel
+    std::deque<PendingPub> pend;         // descriptor copies not yet published
+    std::vector<cudaEvent_t> pub_events; // free events for them
     uint32_t *h_one = nullptr;           // pinned source of those copies
     std::vector<StreamState> st;
     int err = ACS_OK;
@@ -244,7 +253,7 @@ void fill_params(acs_ctx *c, KParams &P) {
     P.sched_smem = sched_smem_bytes(c->W);
     P.poll_ns = c->cfg.poll_ns ? c->cfg.poll_ns : 128u;
     P.mbox = c->d_mbox;
-    P.host_recs = c->d_hring;
+    P.mirror = c->d_mirror;
     P.idle_limit_ns = (unsigned long long)(c->cfg.idle_limit_ms ? c->cfg.idle_limit_ms : 10000u) * 1000000ull;
 }
 
@@ -315,17 +324,57 @@ int resident_status(acs_ctx *c) {
     return ACS_OK;
 }
 
+// Publish the ends of every resident flush whose descriptor copy completed,
+// oldest first (wait: block on each copy).
+int publish_ready(acs_ctx *c, bool wait) {
+    while (!c->pend.empty()) {
+        PendingPub &pp = c->pend.front();
+        const cudaError_t q = wait ? cudaEventSynchronize(pp.ev) : cudaEventQuery(pp.ev);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) return cuda_fail(c, q);
+        // the descriptors are in the device ring; this store publishes them
+        for (auto &se : pp.ends) __atomic_store_n(&c->h_mbox->host_end[se.first], se.second, __ATOMIC_RELEASE);
+        c->pub_events.push_back(pp.ev);
+        c->pend.pop_front();
+    }
+    return ACS_OK;
+}
+
 int flush_resident(acs_ctx *c) {
     int rc = resident_status(c);
     if (rc) return rc;
+    PendingPub pp{};
     for (uint32_t s = 0; s < c->S; ++s) {
         StreamState &ss = c->st[s];
         if (ss.submitted == ss.flushed) continue;
-        // the descriptors are in the pinned ring; this store publishes them
-        __atomic_store_n(&c->h_mbox->host_end[s], ss.submitted, __ATOMIC_RELEASE);
+        uint32_t a = ss.flushed;
+        while (a != ss.submitted) {
+            const uint32_t pa = a & (c->C - 1);
+            const uint32_t n = std::min(ss.submitted - a, c->C - pa);
+            const size_t off = (size_t)s * c->C + pa;
+            cudaError_t e = cudaMemcpyAsync(c->d_ring + off, c->h_ring + off, (size_t)n * sizeof(TaskRec),
+                                            cudaMemcpyHostToDevice, c->side);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            a += n;
+        }
+        pp.ends.emplace_back(s, ss.submitted);
     }
+    if (!pp.ends.empty()) {
+        if (c->pub_events.empty()) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            c->pub_events.push_back(ev);
+        }
+        pp.ev = c->pub_events.back();
+        c->pub_events.pop_back();
+        cudaError_t e = cudaEventRecord(pp.ev, c->side);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->pend.push_back(std::move(pp));
+    }
+    rc = publish_ready(c, false);
     heartbeat(c);
-    return ACS_OK;
+    return rc;
 }
 
 // ---- software scheduler (ACS_MODE_SW) ---------------------------------------------
@@ -629,10 +678,13 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_sched_stats);
     cudaFree(c->d_trace);
     cudaFree(c->d_sctl);
+    cudaFree(c->d_mirror);
     if (c->h_ring) cudaFreeHost(c->h_ring);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_mbox) cudaFreeHost(c->h_mbox);
     if (c->h_one) cudaFreeHost(c->h_one);
+    for (auto &pp : c->pend) c->pub_events.push_back(pp.ev);
+    for (auto ev : c->pub_events) cudaEventDestroy(ev);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -692,7 +744,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
         c->own_stream = true;
     }
     const size_t nrec = (size_t)c->S * c->C;
-    chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocMapped));
+    chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocDefault));
     chk(cudaMalloc(&c->d_ring, nrec * sizeof(TaskRec)));
     chk(cudaMalloc(&c->d_ctl, sizeof(DevCtl)));
     const uint32_t nslots = c->S * kMaxWindow;
@@ -713,6 +765,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMalloc(&c->d_log_retire, nlog * sizeof(unsigned long long)));
     chk(cudaMalloc(&c->d_sched_stats, c->S * sizeof(SchedStats)));
     chk(cudaMalloc(&c->d_sctl, c->S * sizeof(StreamCtl)));
+    chk(cudaMalloc(&c->d_mirror, sizeof(Mirror)));
     chk(cudaHostAlloc(&c->h_status, sizeof(HostStatus), cudaHostAllocMapped));
     chk(cudaHostAlloc(&c->h_mbox, sizeof(Mailbox), cudaHostAllocMapped));
     chk(cudaHostAlloc(&c->h_one, sizeof(uint32_t), cudaHostAllocDefault));
@@ -722,7 +775,6 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     *c->h_one = 1u;
     chk(cudaHostGetDevicePointer((void **)&c->d_status, (void *)c->h_status, 0));
     chk(cudaHostGetDevicePointer((void **)&c->d_mbox, (void *)c->h_mbox, 0));
-    chk(cudaHostGetDevicePointer((void **)&c->d_hring, (void *)c->h_ring, 0));
     chk(cudaMemsetAsync(c->d_sched_stats, 0, c->S * sizeof(SchedStats), c->stream));
     chk(cudaMemsetAsync(c->d_sctl, 0, c->S * sizeof(StreamCtl), c->stream));
     chk(cudaMemsetAsync(c->d_log_mask, 0, nlog * sizeof(unsigned long long), c->stream));
@@ -931,6 +983,8 @@ int sync_resident(acs_ctx *c) {
     while (true) {
         int rc = resident_status(c);
         if (rc) return rc;
+        rc = publish_ready(c, false);
+        if (rc) return rc;
         bool all = true, moved = false;
         for (uint32_t s = 0; s < c->S; ++s) {
             refresh_stream(c, s);
@@ -1062,6 +1116,11 @@ int acs_start(acs_ctx *c) {
         m->progress[s].head = m->progress[s].idle_at = c->st[s].flushed;
     }
     __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    Mirror mir;
+    std::memset(&mir, 0, sizeof mir);
+    for (uint32_t s = 0; s < c->S; ++s) mir.end[s] = c->st[s].flushed;
+    e = cudaMemcpy(c->d_mirror, &mir, sizeof mir, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e);
     KParams P;
     fill_params(c, P);
     P.resident = 1;
@@ -1069,6 +1128,10 @@ int acs_start(acs_ctx *c) {
         P.first[s] = c->st[s].flushed;
         P.end[s] = c->st[s].flushed;
         P.open[s] = 0;
+    }
+    if (!c->side) {
+        e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e);
     }
     int rc = launch_persistent(c, P);
     if (rc) return rc;
@@ -1087,6 +1150,8 @@ int acs_progress(acs_ctx *c, uint32_t *head, uint32_t *idle_at) {
         return c->err;
     }
     heartbeat(c);
+    int prc = publish_ready(c, false);
+    if (prc) return prc;
     for (uint32_t s = 0; s < c->S; ++s) {
         refresh_stream(c, s);
         if (head) head[s] = __atomic_load_n(&c->h_mbox->progress[s].head, __ATOMIC_ACQUIRE);
@@ -1101,6 +1166,7 @@ int acs_stop(acs_ctx *c) {
     using clk = std::chrono::steady_clock;
     // publish what is staged, then ask every scheduler to leave once idle
     if (!c->err) acs_flush(c);
+    publish_ready(c, true);
     __atomic_store_n(&c->h_mbox->drain, 1u, __ATOMIC_RELEASE);
     heartbeat(c);
     auto last = clk::now();

@@ -403,10 +403,25 @@ class _Batch:
         self._pristine.append(keep)
 
     def reset(self) -> None:
-        """Restore every written buffer to the stream's initial state (device copies)."""
+        """Restore every written buffer to the stream's initial state: device
+        copies, or, while a resident kernel holds every SM (a device-to-device
+        copy would wait for it), copies from pinned host memory."""
+        if self.ctx is not None and self.ctx.resident:
+            for (_, _, bufs, _), keep in zip(self.items, self.host_written()):
+                for k, v in keep.items():
+                    bufs.t[k].copy_(v, non_blocking=True)
+            return
         for (_, _, bufs, _), keep in zip(self.items, self._pristine):
             for k, v in keep.items():
                 bufs.t[k].copy_(v, non_blocking=True)
+
+    def host_written(self):
+        """Pinned host copies of each stream's written buffers, initial state
+        (create them before a resident kernel starts: pinning is slow)."""
+        if self._written is None:
+            self._written = [{k: torch.from_numpy(np.ascontiguousarray(host[k]).view(np.uint8).copy()).pin_memory()
+                              for k in WRITTEN[kind] if k in host} for kind, host, _, _ in self.items]
+        return self._written
 
     def host_inputs(self):
         if self._pinned is None:
@@ -445,7 +460,7 @@ class _Batch:
     def _init_common(self, specs, ctx) -> None:
         self.specs, self.ctx = specs, ctx
         self.items, self._pristine = [], []
-        self._pinned = self._results = None
+        self._pinned = self._results = self._written = None
 
     @staticmethod
     def _dnn(sp):
@@ -490,10 +505,24 @@ class BatchedWorkload(_Batch):
                 self.ctx.submit_packed(ids + np.uint32(self.ctx.tail(i)), packed, stream=i)
 
     def run(self) -> int:
-        """One pass over every stream (one flush); returns tasks run."""
+        """One pass over every stream; returns tasks run. With an ordinary
+        context: one flush, one launch. With a resident context: each stream
+        is published as soon as it is submitted, longest first, so the kernel
+        runs the long chains while the host still submits the short ones."""
         before = [self.ctx.tail(i) for i in range(len(self.items))]
-        self.submit_all()
-        self.ctx.flush()
+        if self.ctx.resident:
+            torch.cuda.current_stream().synchronize()    # resets and uploads are on the device
+            for i in sorted(range(len(self.items)), key=lambda k: -self.specs[k].target):
+                kind, _, _, drv = self.items[i]
+                if kind == "rl":
+                    drv.submit()
+                else:
+                    ids, packed = drv
+                    self.ctx.submit_packed(ids + np.uint32(self.ctx.tail(i)), packed, stream=i)
+                self.ctx.flush()
+        else:
+            self.submit_all()
+            self.ctx.flush()
         self.ctx.sync()
         return sum(self.ctx.tail(i) - b for i, b in enumerate(before))
 
