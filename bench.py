@@ -45,7 +45,7 @@ sys.path.insert(0, ROOT)
 METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
 WORKLOAD_DNN = ("dynamic DNN: gated residual MLP, hidden 256, 24 blocks, shared weights; 100 inputs for each "
-                "batch size 1, 2, 4, 8, one flush (one launch) per input, window 32")
+                "batch size 1, 2, 4, 8, one flush per input, window 32")
 WORKLOAD_STATIC = ("static irregular DAG: randomly wired network, 3 stages x 32 nodes (GEMV 256x256 of 1-8 CTAs, "
                    "bias+ReLU, input aggregation), 411 tasks per input, 100 inputs per step, window 32")
 WORKLOAD_SERVING = ("serving: Poisson arrivals of rigid-sphere (64 envs, device-side emission) / gated-MLP "
@@ -408,7 +408,12 @@ class RLBench:
 
 
 def l2_flush(buf):
-    if buf is not None:
+    """Between timed steps: a 512 MiB write (or the given flush function)."""
+    if buf is None:
+        return
+    if callable(buf):
+        buf()
+    else:
         buf.zero_()
 
 
@@ -483,14 +488,29 @@ class BatchArm:
         return n
 
 
+_PINNED_FLUSH = None
+
+
+def copy_engine_flush(torch, flush_buf):
+    """An L2 flush that needs no SM: a host-to-device copy of 512 MiB (while
+    a resident kernel holds every SM, a fill kernel would wait for it)."""
+    global _PINNED_FLUSH
+    if _PINNED_FLUSH is None:
+        _PINNED_FLUSH = torch.empty(flush_buf.numel(), dtype=torch.uint8).pin_memory()
+    return lambda: flush_buf.copy_(_PINNED_FLUSH, non_blocking=True)
+
+
 class DNNInputs:
     """The dynamic-DNN workload: inputs of a gated MLP with shared weights,
-    run one input per flush (the DAG of each input depends on its gates)."""
+    run one input per flush (the DAG of each input depends on its gates).
+    resident: the scheduler kernel stays on the device and every input is
+    published to it (no launch per input); the activations are reset from
+    pinned host memory (a device-side copy would wait for the kernel)."""
 
-    def __init__(self, torch, mode, window, cta_slots, seed=1, per_b=100):
+    def __init__(self, torch, mode, window, cta_slots, seed=1, per_b=100, resident=False):
         import streamgen as sg
         from paper_2401_12377_b300 import harness
-        self.torch = torch
+        self.torch, self.resident = torch, resident
         shared = sg.dnn_weights(seed * 7919, 24)
         self.shared = shared
         self.streams = [sg.dnn_stream(seed * 100000 + b * 1000 + i, batch=b, blocks=24, weight_sets=24,
@@ -506,8 +526,14 @@ class DNNInputs:
             b.dtype.update({"W": np.dtype(np.float32), "B": np.dtype(np.float32)})
             self.bufs.append(b)
             self.packed.append(harness.pack_tasks(st.tasks, b))
-        self.pristine = [{k: b.t[k].clone() for k in ("h", "t", "u")} for b in self.bufs]
-        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots)
+        if resident:
+            self.pristine = [{k: torch.from_numpy(st.buffers[k].view(np.uint8).copy()).pin_memory()
+                              for k in ("h", "t", "u")} for st in self.streams]
+        else:
+            self.pristine = [{k: b.t[k].clone() for k in ("h", "t", "u")} for b in self.bufs]
+        torch.cuda.current_stream().synchronize()
+        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots,
+                                   resident=resident)
         self.n_tasks = sum(len(st.tasks) for st in self.streams)
 
     def reset_device(self):
@@ -516,6 +542,8 @@ class DNNInputs:
                 b.t[k].copy_(v, non_blocking=True)
 
     def run_once(self, latencies=None):
+        if self.resident:
+            self.torch.cuda.current_stream().synchronize()   # resets are on the device
         n = 0
         for ids, rows in self.packed:
             t0 = time.perf_counter()
@@ -529,10 +557,14 @@ class DNNInputs:
         return n
 
 
-def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+def per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, make, workload, extra_l2,
+                    baselines, e2e_fn, oracle_fn):
+    """One input per flush, each with a persistent launch of its own (the
+    line's value); beside it the same flushes published to a resident kernel,
+    then the baselines."""
     W = args.window or 32
     seed = 1 + rank
-    arm = DNNInputs(torch, "window", W, args.cta_slots, seed)
+    arm = make("window", W, seed, False)
     lat = []
     if dist:
         dist.barrier()
@@ -542,31 +574,60 @@ def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     ms_step = statistics.mean(res["ms"])
     max_ms = max_over_ranks(ms_step, dist, "cuda")
     tps = res["tasks"] / args.steps
+    lus = np.sort(np.array(lat)) * 1e6
     st = res["stats"]
     launches = st["launches"]
     avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
     bpl = st["device_seg_bytes"] / max(1, launches)
     achieved = bpl / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6400.0))
-    lus = np.sort(np.array(lat)) * 1e6
+    e2e = e2e_fn(arm)
+    arm.ctx.close()
     line = {"metric": METRIC, "value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DNN, "window": W, "inputs_per_step": len(arm.streams),
+            "config": {"workload": workload, "window": W, "inputs_per_step": len(lat) // args.steps,
                        "tasks_per_step": tps, "cta_slots": st.get("cta_slots"),
-                       "l2": "flushed between timed steps (512 MiB write)",
+                       "mode": "window scheduler, one flush and one persistent launch per input",
+                       "l2": "flushed between timed steps (512 MiB write)" + extra_l2,
                        "parallelism": f"replicas x{world}" if world > 1 else "one GPU"},
             "input_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": bpl, "avg_launch_us": avg_launch_s * 1e6},
-            "gpu_launches": int(launches), "clocks": clocks}
+            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
+    k = max(1, min(args.steps, 3))
+    # the same inputs published to a resident kernel (no launch per input); its
+    # publication path (copy engine, completion seen by the host, device
+    # mirror) costs tens of microseconds per input
+    flush_ce = copy_engine_flush(torch, flush_buf)
+    ra = make("window", W, seed, True)
+    rlat = []
+    rr = time_arm(ra, k, 1, flush_ce, rlat)
+    ra.ctx.close()
+    rms = statistics.mean(rr["ms"])
+    rl = np.sort(np.array(rlat)) * 1e6
+    line["resident_per_input"] = {"tasks_per_s": (rr["tasks"] / k) / (rms / 1e3), "ms_per_step": rms,
+                                  "input_latency_us": {"p50": float(rl[len(rl) // 2]),
+                                                       "p99": float(rl[int(0.99 * (len(rl) - 1))])}}
     if not args.no_baselines:
+        baselines(line, ms_step, k, W, seed)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_fn(arm)
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    return line
+
+
+def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+    def make(mode, W, seed, resident):
+        return DNNInputs(torch, mode, W, args.cta_slots, seed, resident=resident)
+
+    def baselines(line, ms_step, k, W, seed):
         for mode in ("inorder", "graph", "sw"):
-            b = DNNInputs(torch, mode, W, args.cta_slots, seed)
-            r = time_arm(b, max(1, min(args.steps, 3)), 1, flush_buf)
+            b = make(mode, W, seed, False)
+            r = time_arm(b, k, 1, flush_buf)
             ms = statistics.mean(r["ms"])
-            k = max(1, min(args.steps, 3))
             entry = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms,
                      "kernel_ms_per_step": r["stats"]["kernel_ms"] / k}
             if mode == "graph":
@@ -584,32 +645,35 @@ def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                 line["inorder"] = entry
                 line["speedup_vs_inorder"] = ms / ms_step
             b.ctx.close()
-    # end to end: each input's activations in from pinned memory, its output h back
-    pin_in = [{k: torch.from_numpy(st.buffers[k].view(np.uint8).copy()).pin_memory() for k in ("h", "t", "u")}
-              for st in arm.streams]
-    pin_out = [torch.empty(b.t["h"].numel(), dtype=torch.uint8).pin_memory() for b in arm.bufs]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    h2d = d2h = n = 0
-    for (ids, rows), b, pi, po in zip(arm.packed, arm.bufs, pin_in, pin_out):
-        for k, v in pi.items():
-            b.t[k].copy_(v, non_blocking=True)
-            h2d += v.numel()
-        start = arm.ctx.tail(0)
-        arm.ctx.submit_packed(ids + np.uint32(start), rows)
-        arm.ctx.flush()
-        arm.ctx.sync()
-        po.copy_(b.t["h"], non_blocking=True)
-        d2h += po.numel()
-        n += len(ids)
-    ev1.record()
-    torch.cuda.synchronize()
-    e_ms = ev0.elapsed_time(ev1)
-    line["e2e"] = {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
-                   "h2d_bytes_per_step": int(h2d + 320 * n), "d2h_bytes_per_step": int(d2h)}
-    arm.ctx.close()
-    if rank == 0 and world == 1 and not args.no_cpu:
+
+    def e2e(arm):
+        # each input's activations in from pinned memory, its output h back
+        pin_in = [{k: torch.from_numpy(st.buffers[k].view(np.uint8).copy()).pin_memory() for k in ("h", "t", "u")}
+                  for st in arm.streams]
+        pin_out = [torch.empty(b.t["h"].numel(), dtype=torch.uint8).pin_memory() for b in arm.bufs]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.current_stream().synchronize()
+        ev0.record()
+        h2d = d2h = n = 0
+        for (ids, rows), b, pi, po in zip(arm.packed, arm.bufs, pin_in, pin_out):
+            for k, v in pi.items():
+                b.t[k].copy_(v, non_blocking=True)
+                h2d += v.numel()
+            if arm.resident:
+                torch.cuda.current_stream().synchronize()
+            arm.ctx.submit_packed(ids + np.uint32(arm.ctx.tail(0)), rows)
+            arm.ctx.flush()
+            arm.ctx.sync()
+            po.copy_(b.t["h"], non_blocking=True)
+            d2h += po.numel()
+            n += len(ids)
+        ev1.record()
+        torch.cuda.current_stream().synchronize()
+        e_ms = ev0.elapsed_time(ev1)
+        return {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                "h2d_bytes_per_step": int(h2d + 320 * n), "d2h_bytes_per_step": int(d2h)}
+
+    def oracle(arm):
         from oracle import execute
         t0 = time.perf_counter()
         n = k = 0
@@ -619,30 +683,34 @@ def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             n += len(st.tasks)
             k += 1
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
-                                "sample": f"first {k} inputs of the step ({n} tasks), single-threaded numpy, "
-                                          f"{dt:.1f} s"}
-    elif rank == 0:
-        line["cpu_baseline"] = None
-    return line
+        return {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                "sample": f"first {k} inputs of the step ({n} tasks), single-threaded numpy, {dt:.1f} s"}
+
+    return per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, make, WORKLOAD_DNN, "",
+                           baselines, e2e, oracle)
 
 
 class StaticInputs:
     """The static randomly wired network: one task graph, 100 inputs per
     step. The window scheduler and the in-order / software baselines run
     every input as its own flush; the CUDA graph is built for the first input
-    and replayed for every later one (inputs change only the data)."""
+    and replayed for every later one (inputs change only the data). resident:
+    the scheduler kernel stays on the device, each input is copied in from
+    pinned host memory and then published."""
 
-    def __init__(self, torch, mode, window, cta_slots, seed=1, n_inputs=100):
+    def __init__(self, torch, mode, window, cta_slots, seed=1, n_inputs=100, resident=False):
         import streamgen as sg
         from paper_2401_12377_b300 import harness
-        self.torch, self.mode = torch, mode
+        self.torch, self.mode, self.resident = torch, mode, resident
         self.stream = sg.random_wire_stream(seed, window=window)
         self.bufs = harness.DeviceBuffers(self.stream.buffers)
         rng = np.random.default_rng(seed + 17)
-        self.inputs = torch.from_numpy(rng.uniform(-1, 1, (n_inputs, 256)).astype(np.float32)).cuda()
+        host_in = rng.uniform(-1, 1, (n_inputs, 256)).astype(np.float32)
+        self.inputs = torch.from_numpy(host_in).pin_memory() if resident else torch.from_numpy(host_in).cuda()
         self.ids, self.rows = harness.pack_tasks(self.stream.tasks, self.bufs)
-        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots)
+        torch.cuda.current_stream().synchronize()
+        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots,
+                                   resident=resident)
         self.x0 = self.bufs.t["x"][:1024].view(torch.float32)
         self.built = False
 
@@ -654,6 +722,8 @@ class StaticInputs:
         for i in range(self.inputs.shape[0]):
             t0 = time.perf_counter()
             self.x0.copy_(self.inputs[i], non_blocking=True)
+            if self.resident:
+                self.torch.cuda.current_stream().synchronize()   # the input is on the device
             if self.mode == "graph" and self.built:
                 self.ctx.replay()
             else:
@@ -668,41 +738,12 @@ class StaticInputs:
 
 
 def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
-    W = args.window or 32
-    seed = 1 + rank
-    arm = StaticInputs(torch, "window", W, args.cta_slots, seed)
-    lat = []
-    if dist:
-        dist.barrier()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        res = time_arm(arm, args.steps, args.warmup, flush_buf, lat)
-    clocks = clk.summary()
-    ms_step = statistics.mean(res["ms"])
-    max_ms = max_over_ranks(ms_step, dist, "cuda")
-    tps = res["tasks"] / args.steps
-    st = res["stats"]
-    launches = st["launches"]
-    avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
-    bpl = st["device_seg_bytes"] / max(1, launches)
-    achieved = bpl / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-    peak = float(peaks.get("hbm_gbs", 6400.0))
-    lus = np.sort(np.array(lat)) * 1e6
-    line = {"metric": METRIC, "value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_STATIC, "window": W, "inputs_per_step": arm.inputs.shape[0],
-                       "tasks_per_step": tps, "cta_slots": st.get("cta_slots"),
-                       "l2": "flushed between timed steps (512 MiB write); 24 MB of weights per input",
-                       "parallelism": f"replicas x{world}" if world > 1 else "one GPU"},
-            "input_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": bpl, "avg_launch_us": avg_launch_s * 1e6},
-            "gpu_launches": int(launches), "clocks": clocks}
-    if not args.no_baselines:
-        k = max(1, min(args.steps, 3))
+    def make(mode, W, seed, resident):
+        return StaticInputs(torch, mode, W, args.cta_slots, seed, resident=resident)
+
+    def baselines(line, ms_step, k, W, seed):
         for mode in ("inorder", "graph", "sw"):
-            b = StaticInputs(torch, mode, W, args.cta_slots, seed)
+            b = make(mode, W, seed, False)
             r = time_arm(b, k, 1, flush_buf)
             ms = statistics.mean(r["ms"])
             entry = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms,
@@ -711,7 +752,6 @@ def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                 entry["note"] = "graph built once (first warm-up input), replayed for every input"
                 line["graph_replay"] = entry
                 line["speedup_vs_graph_replay"] = ms / ms_step
-                line["speedup_vs_graph_replay_device_only"] = entry["kernel_ms_per_step"] / (st["kernel_ms"] / args.steps)
             elif mode == "sw":
                 line["sw_host_scheduler"] = entry
                 line["speedup_vs_sw_host_scheduler"] = ms / ms_step
@@ -719,28 +759,32 @@ def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                 line["inorder"] = entry
                 line["speedup_vs_inorder"] = ms / ms_step
             b.ctx.close()
-    # end to end: each input in from pinned memory, the stage output back
-    pin_in = arm.inputs.cpu().pin_memory()
-    pin_out = torch.empty(256, dtype=torch.float32).pin_memory()
-    xout = arm.bufs.t["x"].view(torch.float32)[-256:]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    n = 0
-    for i in range(pin_in.shape[0]):
-        arm.x0.copy_(pin_in[i], non_blocking=True)
-        arm.ctx.submit_packed(arm.ids + np.uint32(arm.ctx.tail(0)), arm.rows)
-        arm.ctx.flush()
-        arm.ctx.sync()
-        pin_out.copy_(xout, non_blocking=True)
-        n += len(arm.ids)
-    ev1.record()
-    torch.cuda.synchronize()
-    e_ms = ev0.elapsed_time(ev1)
-    line["e2e"] = {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
-                   "h2d_bytes_per_step": int(pin_in.numel() * 4 + 320 * n), "d2h_bytes_per_step": int(1024 * pin_in.shape[0])}
-    arm.ctx.close()
-    if rank == 0 and world == 1 and not args.no_cpu:
+
+    def e2e(arm):
+        # each input in from pinned memory (every timed input already is), the stage output back
+        pin_out = torch.empty(256, dtype=torch.float32).pin_memory()
+        xout = arm.bufs.t["x"].view(torch.float32)[-256:]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.current_stream().synchronize()
+        ev0.record()
+        n = 0
+        for i in range(arm.inputs.shape[0]):
+            arm.x0.copy_(arm.inputs[i], non_blocking=True)
+            if arm.resident:
+                torch.cuda.current_stream().synchronize()
+            arm.ctx.submit_packed(arm.ids + np.uint32(arm.ctx.tail(0)), arm.rows)
+            arm.ctx.flush()
+            arm.ctx.sync()
+            pin_out.copy_(xout, non_blocking=True)
+            n += len(arm.ids)
+        ev1.record()
+        torch.cuda.current_stream().synchronize()
+        e_ms = ev0.elapsed_time(ev1)
+        return {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                "h2d_bytes_per_step": int(arm.inputs.numel() * 4 + 320 * n),
+                "d2h_bytes_per_step": int(1024 * arm.inputs.shape[0])}
+
+    def oracle(arm):
         from oracle import execute
         t0 = time.perf_counter()
         n = k = 0
@@ -749,11 +793,11 @@ def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             n += len(arm.stream.tasks)
             k += 1
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{k} inputs ({n} tasks), single-threaded numpy, {dt:.1f} s"}
-    elif rank == 0:
-        line["cpu_baseline"] = None
-    return line
+        return {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                "sample": f"{k} inputs ({n} tasks), single-threaded numpy, {dt:.1f} s"}
+
+    return per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, make, WORKLOAD_STATIC,
+                           "; 24 MB of weights per input", baselines, e2e, oracle)
 
 
 def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):

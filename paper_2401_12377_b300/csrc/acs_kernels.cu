@@ -335,10 +335,10 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
             if (lds_volatile(&S.sh->quit)) return;
             if (host_wait) {
                 // waiting for the host is not a stall: the scheduler warp bounds
-                // it (idle limit) and raises quit; poll the bus every ~2 us
+                // it (idle limit) and raises quit; the mirror is device memory
                 tw = 0;
                 __nanosleep(backoff);
-                if (backoff < 2048) backoff <<= 1;
+                if (backoff < 512) backoff <<= 1;
                 continue;
             }
             if ((++spins & 63) == 0) {
@@ -851,10 +851,10 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             idle_sleep = 256;
         } else if (idle) {
             // resident and waiting for the host: bounded by the idle limit
-            // above; the sleep grows to 8 us so idle streams stay quiet
+            // above (the polls stay in device memory and take no fence)
             idle_since = 0;
             __nanosleep(idle_sleep);
-            if (idle_sleep < 8192) idle_sleep <<= 1;
+            if (idle_sleep < 1024) idle_sleep <<= 1;
         } else {
             const unsigned long long now = globaltimer_ns();
             if (idle_since == 0) idle_since = now;

@@ -980,7 +980,8 @@ int sync_resident(acs_ctx *c) {
     using clk = std::chrono::steady_clock;
     auto last = clk::now();
     std::vector<uint32_t> seen(c->S, 0);
-    while (true) {
+    // spin first (short requests finish in microseconds), then poll every 20 us
+    for (uint32_t iter = 0;; ++iter) {
         int rc = resident_status(c);
         if (rc) return rc;
         rc = publish_ready(c, false);
@@ -994,6 +995,8 @@ int sync_resident(acs_ctx *c) {
             if (ss.emitting || ss.synced != ss.flushed) all = false;
         }
         if (all) return ACS_OK;
+        const bool spinning = iter < 4096;
+        if (spinning && (iter & 63) != 0) continue;
         heartbeat(c);
         const cudaError_t q = cudaStreamQuery(c->stream);
         if (q != cudaErrorNotReady) {     // the kernel is gone before the work retired
@@ -1004,7 +1007,7 @@ int sync_resident(acs_ctx *c) {
         else if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - last).count() >
                  c->cfg.timeout_ns)
             return fail(c, ACS_ERR_TIMEOUT);
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (!spinning) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
