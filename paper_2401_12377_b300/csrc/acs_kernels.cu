@@ -624,7 +624,36 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         if (open) end = lds_volatile(&S.sh->end);
 
         ACS_PHASE(0);
-        // 1. how many tasks are checked and have a free slot (at most 32 per
+        const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
+        // 1. retire the slots the poller warp saw complete, first, so that a
+        //    slot released now takes a task in this same iteration
+        unsigned long long R = 0;
+        if (lane == 0) R = atomicExch(S.retired, 0ull);
+        R = ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(R >> 32), 0) << 32) |
+            __shfl_sync(0xffffffffu, (uint32_t)R, 0);
+        const bool ret0 = (R >> lane) & 1ull;
+        const bool ret1 = W > 32 && ((R >> (lane + 32)) & 1ull);
+        if (R) {
+            progress = true;
+            if (ret0) st0 = kRetired;
+            if (ret1) st1 = kRetired;
+            if (tracing) {
+                const unsigned long long now = globaltimer_ns();
+                if (ret0) P.trace[(lbase + (sq0 & LM)) * kTraceFields + 4] = now;
+                if (ret1) P.trace[(lbase + (sq1 & LM)) * kTraceFields + 4] = now;
+            }
+            // release in program order: the run of retired slots from the head
+            unsigned long long RT = __ballot_sync(0xffffffffu, st0 == kRetired);
+            if (W > 32) RT |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kRetired) << 32;
+            const unsigned long long rrt = hslot ? (((RT >> hslot) | (RT << (W - hslot))) & full) : RT;
+            uint32_t run = rrt == ~0ull ? 64u : (uint32_t)(__ffsll((long long)~rrt) - 1);
+            run = min(run, next - head);
+            head += run;
+            hslot += run;
+            if (hslot >= W) hslot -= W;
+        }
+        ACS_PHASE(2);
+        // 2. how many tasks are checked and have a free slot (at most 32 per
         //    iteration); one CTA-scope fence orders the tag reads before the
         //    mask reads (before the global polls below, so it never waits on them)
         uint32_t nins = 0;
@@ -647,12 +676,11 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         }
         if (nins) __threadfence_block();
 
-        const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
-        // values of this iteration's insertion batch, published after retire
+        // values of this iteration's insertion batch, handed to the publisher below
         bool mine = false;
         uint32_t q = 0, my_n = 0, my_off = 0, js = 0, p0 = 0, total = 0;
         unsigned long long my_up = 0;
-        // 2. insert and dispatch, lane k taking task next + k. Every task is
+        // 3. insert and dispatch, lane k taking task next + k. Every task is
         //    dispatched when it enters the window: its worker CTAs wait for the
         //    checker's mask and then for the done words of the predecessors it
         //    names. Units enter the FIFO work ring in program order, after
@@ -663,7 +691,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             q = next + lane;
             my_n = mine ? (uint32_t)S.hist[q & HM].r.ncta : 0u;
             // upstream = candidates still active (older new tasks included);
-            // retired ones are covered by the release below
+            // retired ones were released above
             unsigned long long act = __ballot_sync(0xffffffffu, st0 == kExec);
             if (W > 32) act |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kExec) << 32;
             const unsigned long long pre = mine ? S.pmask[q & HM] : 0ull;
@@ -725,35 +753,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             __syncwarp();
         }
         ACS_PHASE(1);
-
-        // 4. retire the slots the poller warp saw complete
-        unsigned long long R = 0;
-        if (lane == 0) R = atomicExch(S.retired, 0ull);
-        R = ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(R >> 32), 0) << 32) |
-            __shfl_sync(0xffffffffu, (uint32_t)R, 0);
-        const bool ret0 = (R >> lane) & 1ull;
-        const bool ret1 = W > 32 && ((R >> (lane + 32)) & 1ull);
-        if (R) {
-            progress = true;
-            if (ret0) st0 = kRetired;
-            if (ret1) st1 = kRetired;
-            if (tracing) {
-                const unsigned long long now = globaltimer_ns();
-                if (ret0) P.trace[(lbase + (sq0 & LM)) * kTraceFields + 4] = now;
-                if (ret1) P.trace[(lbase + (sq1 & LM)) * kTraceFields + 4] = now;
-            }
-            // release in program order: the run of retired slots from the head
-            unsigned long long RT = __ballot_sync(0xffffffffu, st0 == kRetired);
-            if (W > 32) RT |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kRetired) << 32;
-            const unsigned long long rrt = hslot ? (((RT >> hslot) | (RT << (W - hslot))) & full) : RT;
-            uint32_t run = rrt == ~0ull ? 64u : (uint32_t)(__ffsll((long long)~rrt) - 1);
-            run = min(run, next - head);
-            head += run;
-            hslot += run;
-            if (hslot >= W) hslot -= W;
-        }
-        ACS_PHASE(2);
-        // 5. hand this iteration's insertion batch to the publisher warp (its
+        // 4. hand this iteration's insertion batch to the publisher warp (its
         //    fence then orders the log entries above and the retirements seen
         //    through the poller before the new units: conflicts farther back
         //    than W - 1 rely on that alone)
