@@ -1,23 +1,30 @@
 // Device side of the scheduler: one cooperative persistent kernel.
 //
-// CTAs [0, n_streams) are schedulers: warp 0 of CTA s owns stream s. It keeps
-// the stream's scheduling window (W slots, Sec. III-C) in shared memory and the
-// per-slot state machine (pending / ready / executing / retired, Sec. III-C) and
-// upstream masks in registers: lane l holds slots l and l + 32. Warp 7 streams
-// descriptors into a shared-memory history ring ahead of use; warps 1..6 run
-// the segment-overlap test of Alg. 1 (extended to read-after-write) of each
-// task against its W - 1 predecessors, one predecessor per lane, and a ballot
-// turns the per-lane results into the task's upstream-candidate mask. Warp 0
-// inserts checked tasks (upstream = candidates still active), retires them
-// (mask &= ~retired) and dispatches them oldest first.
+// CTAs [0, n_streams) are schedulers, one per stream, 8 warps each:
+//   warp 0 owns the stream's scheduling window (W slots, Sec. III-C): the
+//          per-slot state machine (pending / ready / executing / retired,
+//          Sec. III-C) and upstream masks live in its registers (lane l holds
+//          slots l and l + 32). Each iteration it retires the slots the poller
+//          saw complete, releases them in program order, and inserts checked
+//          tasks (upstream = candidates still active), oldest first;
+//   warps 1..4 run the segment-overlap test of Alg. 1 (extended to
+//          read-after-write) of each task against its W - 1 predecessors,
+//          one predecessor per lane; a ballot turns the per-lane results into
+//          the task's upstream-candidate mask;
+//   warp 5 publishes each insertion batch to the work ring (aux words, one
+//          fence, the cells' sequence words);
+//   warp 6 polls the done words of executing slots;
+//   warp 7 streams descriptors into a shared-memory history ring ahead of
+//          use (and, in a resident launch, follows the host-published ends).
 //
 // CTAs [n_streams, grid) are workers: each claims work-ring positions one at a
 // time, runs the body for one (task, CTA index) unit, and the last CTA of a
 // task publishes done[slot] = seq + 1 with release semantics.
 //
-// Every wait is bounded by timeout_ns of no progress; on expiry the waiter
-// records ACS_ERR_TIMEOUT, raises the stop flag and leaves, so the kernel
-// always terminates.
+// Every wait is bounded by timeout_ns of no progress (a resident launch's
+// waits for the host by its idle limit); on expiry the waiter records
+// ACS_ERR_TIMEOUT, raises the stop flag and leaves, so the kernel always
+// terminates.
 #include <cstdint>
 
 #include "acs_bodies.cuh"
@@ -97,6 +104,9 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 //               each conflicting predecessor i in [seq - W + 1, seq - 1])
 //   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
 //   sh          counters shared by the warps
+//   retired     slots the poller saw retire, not yet taken by warp 0
+//   expect[64]  the done value each executing slot waits for (0: none)
+//   pub         the insertion batches handed from warp 0 to the publisher
 //
 // Warps 1..4 ("checkers") compute the upstream-candidate mask of tasks
 // j = first + w + 4k: the segment-overlap test of Alg. 1 (extended to RAW) of
