@@ -147,3 +147,42 @@ def test_autotuner_picks_and_caches(tmp_path):
     again = autotune.tune("test-batched-4", make_run, n_streams=4, path=path)
     assert again["cached"] and again["window"] == res["window"] and again["cta_slots"] == res["cta_slots"]
     assert json.load(open(path))
+
+
+def test_batched_full_size_in_the_benchmarked_configuration():
+    """The full batched workload (64 streams, 82 508 tasks) in the launch
+    configuration bench.py times: one resident kernel, window 8, 232 worker
+    CTAs, streams published longest first. Per stream: the logged window DAG
+    equals the oracle's D_W (built directly over distance W - 1), the ticket
+    log is legal on D_W and keeps the ring's release order (which covers the
+    longer edges of E), and outputs match the oracle."""
+    W = 8
+    specs = sg.batched_specs(1)
+    wl = harness.BatchedWorkload(specs, None)
+    wl.host_written()
+    with harness.Context(W, n_streams=len(specs), cta_slots=232, log=True, capacity=1 << 13,
+                         resident=True) as ctx:
+        wl.bind(ctx)
+        n = wl.run()
+        outs = wl.outputs()
+        logs = [ctx.log(i, 0, ctx.tail(i)) for i in range(len(specs))]
+        ctx.stop()
+    total = 0
+    for i, sp in enumerate(specs):
+        o_tasks, o_bufs = _oracle(sp)
+        masks, start, retire = logs[i]
+        assert len(masks) == len(o_tasks), (i, sp.kind)
+        total += len(o_tasks)
+        D = deps.window_dag_direct(addresses.stream_segments(o_tasks, o_bufs), W)
+        assert deps.edges_from_masks([int(x) for x in masks], W) == D, i
+        st, rt = [int(x) for x in start], [int(x) for x in retire]
+        assert not deps.check_legal(D, st, rt), i
+        assert not deps.check_release_order(st, rt, W), i
+        for k in o_bufs:
+            g, o = outs[i][k], o_bufs[k]
+            if sp.kind == "rl" or o.dtype != np.float32:
+                assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
+            else:
+                scale = max(float(np.abs(o).max()), 1e-30)
+                assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+    assert n == total == 82508
