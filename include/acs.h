@@ -314,9 +314,10 @@ int acs_get_log(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n,
 /*
  * Copy the window-mode timestamps (device %globaltimer, ns) of tasks [first,
  * first + n) of `stream` into t[5*n]: for task i, t[5i+0] insertion into the
- * window, t[5i+1] dispatch, t[5i+2] start of its first CTA, t[5i+3] end of its
- * last CTA, t[5i+4] retirement seen by the scheduler. Needs ACS_FLAG_TRACE and
- * a completed acs_sync; same range rules as acs_get_log. Errors: ACS_ERR_INVALID.
+ * window, t[5i+1] publication of its work units to the worker CTAs, t[5i+2]
+ * start of its first CTA, t[5i+3] end of its last CTA, t[5i+4] retirement
+ * seen by the scheduler. Needs ACS_FLAG_TRACE and a completed acs_sync; same
+ * range rules as acs_get_log. Errors: ACS_ERR_INVALID.
  */
 int acs_get_trace(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n, uint64_t *t);
 

@@ -205,7 +205,7 @@ def acs_get_log(ctx, stream: int, first: int, n: int):
 
 
 def acs_get_trace(ctx, stream: int, first: int, n: int) -> np.ndarray:
-    """(n, 5) globaltimer ns: insert, dispatch, first-CTA start, last-CTA end, retire seen."""
+    """(n, 5) globaltimer ns: insert, units published, first-CTA start, last-CTA end, retire seen."""
     t = np.zeros((n, 5), np.uint64)
     check(load().acs_get_trace(ctx, stream, first, n, t.ctypes.data), "acs_get_trace")
     return t

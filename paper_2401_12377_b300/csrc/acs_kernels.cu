@@ -11,9 +11,9 @@
 //          read-after-write) of each task against its W - 1 predecessors,
 //          one predecessor per lane; a ballot turns the per-lane results into
 //          the task's upstream-candidate mask;
-//   warp 5 publishes each insertion batch to the work ring (aux words, one
-//          fence, the cells' sequence words);
-//   warp 6 polls the done words of executing slots;
+//   warp 5 publishes the pending insertion batches to the work ring (aux
+//          words, one fence per pass, the cells' sequence words);
+//   warp 6 polls the done words of executing slots (acquire loads);
 //   warp 7 streams descriptors into a shared-memory history ring ahead of
 //          use (and, in a resident launch, follows the host-published ends).
 //
@@ -365,11 +365,11 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     }
 }
 
-// Warp 6: polls the done word of every executing slot (relaxed loads) and
-// posts the slots whose task retired into a shared bitmask; the acquire fence
-// it executes before posting, with warp 0's fence before it publishes work,
-// orders the retired tasks' writes before every dependent's start. Warp 0
-// never waits on global memory to retire tasks.
+// Warp 6: polls the done word of every executing slot (acquire loads) and
+// posts the slots whose task retired into a shared bitmask; those acquires,
+// with the publisher's fence before it publishes work, order the retired
+// tasks' writes before every dependent's start. Warp 0 never waits on global
+// memory to retire tasks.
 __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
@@ -380,11 +380,13 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
         const uint32_t e0 = lane < W ? lds_volatile(&S.expect[lane]) : 0u;
         const uint32_t e1 = lane + 32 < W ? lds_volatile(&S.expect[lane + 32]) : 0u;
         bool h0 = false, h1 = false;
-        if (e0) h0 = (int32_t)(ld_relaxed_u32(&done[lane]) - e0) >= 0;
-        if (e1) h1 = (int32_t)(ld_relaxed_u32(&done[lane + 32]) - e1) >= 0;
+        // acquire loads: a done word read at its task's value orders the
+        // task's writes before what this lane does next
+        if (e0) h0 = (int32_t)(ld_acquire_u32(&done[lane]) - e0) >= 0;
+        if (e1) h1 = (int32_t)(ld_acquire_u32(&done[lane + 32]) - e1) >= 0;
         const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
         if (b0 | b1) {
-            fence_acq_rel_gpu();                 // acquire: the retired tasks' writes
+            __syncwarp();                        // ... and, among the lanes, before lane 0 posts
             if (h0) sts_volatile(&S.expect[lane], 0u);
             if (h1) sts_volatile(&S.expect[lane + 32], 0u);
             __threadfence_block();
@@ -509,83 +511,113 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     }
 }
 
-// Warp 5: publishes the scheduler's insertion batches, oldest first. Per
-// batch: each task's aux word (upstream still to wait for, seq), a check that
-// every work-ring cell it fills is free (its sequence word reads its
-// position), one fence.acq_rel.gpu, then the cells' sequence words. The fence
-// orders what the scheduler warp wrote or saw before handing the batch over
-// (log entries; retirements the poller acquired) before the new units.
+// Warp 5: publishes the scheduler's insertion batches, oldest first, every
+// batch pending at the time in one pass: each task's aux word (upstream still
+// to wait for, seq) and a check that every work-ring cell it fills is free (its
+// sequence word reads its position), one fence.acq_rel.gpu for the pass, then
+// the cells' sequence words. The fence orders what the scheduler warp wrote or
+// saw before handing the batches over (log entries; retirements the poller
+// acquired) before the new units. A pass costs about one fence whatever the
+// number of batches, so batches that queue while one is published go out
+// together in the next.
 __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t C = 1u << P.cap_log2;
     SchedSmem S = carve(smem_raw, P.window);
     const bool sole_producer = P.n_streams == 1;
+    const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     uint32_t done_b = 0, backoff = 32;
-    uint32_t next_p0 = 0;                 // sole producer: where the next batch starts
-    unsigned long long pre0 = 0, pre1 = 0; // ... and its first 64 cells as last read
+    // sole producer: batches fill consecutive positions; after each pass the
+    // sequence words of the kPreCells cells from pre_base on are read (lane l
+    // holds base + l + 32 k in pre[k]) for the checks of the next pass
+    constexpr uint32_t kPreCells = 128;
+    uint32_t pre_base = 0, pre0 = 0, pre1 = 0, pre2 = 0, pre3 = 0;
     bool have_pre = false;
     while (true) {
         const uint32_t prod = lds_volatile(&S.pub->produced);
         if (prod == done_b) {
             if (lds_volatile(&S.sh->quit)) return;
             __nanosleep(backoff);
-            if (backoff < 128) backoff <<= 1;
+            if (backoff < 64) backoff <<= 1;
             continue;
         }
         backoff = 32;
         __threadfence_block();
-        const PubBatch &B = S.pub->b[done_b % kPubSlots];
-        const uint32_t nins = B.nins, p0 = B.p0, total = B.total;
-        const bool mine = lane < nins;
-        uint32_t q = 0, off = 0, n = 0, gidx = 0;
-        if (mine) {
-            q = B.q[lane];
-            off = B.off[lane];
-            n = B.n[lane];
-            gidx = (stream << P.cap_log2) | (q & (C - 1));
-            const unsigned long long up = B.up[lane];
-            *reinterpret_cast<uint4 *>(&P.taskaux[gidx]) = make_uint4((uint32_t)up, (uint32_t)(up >> 32), q, 0u);
+        // free cells among the prefetched ones, one bit per position
+        uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+        if (have_pre) {
+            f0 = __ballot_sync(0xffffffffu, pre0 == pre_base + lane);
+            f1 = __ballot_sync(0xffffffffu, pre1 == pre_base + 32u + lane);
+            f2 = __ballot_sync(0xffffffffu, pre2 == pre_base + 64u + lane);
+            f3 = __ballot_sync(0xffffffffu, pre3 == pre_base + 96u + lane);
         }
-        // a cell is free for position p once its sequence word reads p
+        // 1. every pending batch: aux words, then its cells checked free
         bool ok = true;
-        const bool pre_ok = sole_producer && have_pre && next_p0 == p0;
-        for (uint32_t u = lane; u < total && ok; u += 32) {
-            if (pre_ok && u < 64 && (uint32_t)(u < 32 ? pre0 : pre1) == p0 + u) continue;
-            unsigned long long *cell = &P.cells[(p0 + u) & P.cell_mask];
-            unsigned long long tw = 0;
-            uint32_t spins = 0;
-            while ((uint32_t)ld_relaxed_u64(cell) != p0 + u) {
-                if ((++spins & 63) == 0) {
-                    const unsigned long long now = globaltimer_ns();
-                    if (tw == 0) tw = now;
-                    else if (now - tw > P.timeout_ns) {
-                        raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
-                        ok = false;
-                        break;
+        uint32_t last_end = 0;
+        for (uint32_t b = done_b; b != prod && ok; ++b) {
+            const PubBatch &B = S.pub->b[b % kPubSlots];
+            const uint32_t nins = B.nins, p0 = B.p0, total = B.total;
+            if (lane < nins) {
+                const uint32_t q = B.q[lane];
+                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
+                const unsigned long long up = B.up[lane];
+                *reinterpret_cast<uint4 *>(&P.taskaux[gidx]) = make_uint4((uint32_t)up, (uint32_t)(up >> 32), q, 0u);
+            }
+            last_end = p0 + total;
+            for (uint32_t u = lane; u < total && ok; u += 32) {
+                const uint32_t x = p0 + u, d = x - pre_base;
+                if (have_pre && d < kPreCells) {
+                    const uint32_t f = d < 32 ? f0 : d < 64 ? f1 : d < 96 ? f2 : f3;
+                    if ((f >> (d & 31)) & 1u) continue;
+                }
+                unsigned long long *cell = &P.cells[x & P.cell_mask];
+                unsigned long long tw = 0;
+                uint32_t spins = 0;
+                while ((uint32_t)ld_relaxed_u64(cell) != x) {
+                    if ((++spins & 63) == 0) {
+                        const unsigned long long now = globaltimer_ns();
+                        if (tw == 0) tw = now;
+                        else if (now - tw > P.timeout_ns) {
+                            raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteRing);
+                            ok = false;
+                            break;
+                        }
+                        if (stopped(P)) { ok = false; break; }
                     }
-                    if (stopped(P)) { ok = false; break; }
                 }
             }
         }
         if (!__all_sync(0xffffffffu, ok)) return;
         fence_acq_rel_gpu();
         __syncwarp();
-        if (mine) {
-            for (uint32_t c = 0; c < n; ++c) {
-                const uint32_t pos = p0 + off + c;
-                const uint32_t payload = (gidx << 8) | c;
-                st_relaxed_u64(&P.cells[pos & P.cell_mask],
-                               ((unsigned long long)payload << 32) | (unsigned long long)(pos + 1u));
+        // 2. the cells of every pending batch
+        for (uint32_t b = done_b; b != prod; ++b) {
+            const PubBatch &B = S.pub->b[b % kPubSlots];
+            const uint32_t nins = B.nins, p0 = B.p0;
+            if (lane < nins) {
+                const uint32_t q = B.q[lane], off = B.off[lane], n = B.n[lane];
+                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
+                if (tracing)   // publication: the units become visible from here on
+                    P.trace[(((size_t)stream << P.log_log2) + (q & ((1u << P.log_log2) - 1u))) * kTraceFields + 1] =
+                        globaltimer_ns();
+                for (uint32_t c = 0; c < n; ++c) {
+                    const uint32_t pos = p0 + off + c;
+                    const uint32_t payload = (gidx << 8) | c;
+                    st_relaxed_u64(&P.cells[pos & P.cell_mask],
+                                   ((unsigned long long)payload << 32) | (unsigned long long)(pos + 1u));
+                }
             }
         }
-        ++done_b;
+        done_b = prod;
         __syncwarp();
         if (lane == 0) sts_volatile(&S.pub->consumed, done_b);
-        // look at the next 64 cells for the following batch (sole producer)
+        // the cells the following batches start on (sole producer)
         if (sole_producer) {
-            next_p0 = p0 + total;
-            pre0 = ld_relaxed_u64(&P.cells[(next_p0 + lane) & P.cell_mask]);
-            pre1 = ld_relaxed_u64(&P.cells[(next_p0 + 32 + lane) & P.cell_mask]);
+            pre_base = last_end;
+            pre0 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + lane) & P.cell_mask]);
+            pre1 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 32u + lane) & P.cell_mask]);
+            pre2 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 64u + lane) & P.cell_mask]);
+            pre3 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 96u + lane) & P.cell_mask]);
             have_pre = true;
         }
     }
@@ -738,8 +770,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                     }
                     if (tracing) {
                         const unsigned long long now = globaltimer_ns();
-                        P.trace[li * kTraceFields + 0] = now;
-                        P.trace[li * kTraceFields + 1] = now;
+                        P.trace[li * kTraceFields + 0] = now;   // field 1: the publisher warp
                         P.trace[li * kTraceFields + 2] = ~0ull;   // first-CTA start: atomicMin target
                     }
                 }
@@ -1076,8 +1107,10 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             uint32_t quit = 0, spins = 0, backoff = 32;
             unsigned long long tw = 0, v;
             while (true) {
-                v = ld_relaxed_u64(cell);
-                if ((uint32_t)v == pos + 1u) { fence_acq_rel_gpu(); break; }
+                // an acquire load: reading the publisher's cell (written after
+                // its fence) orders everything it published before this unit
+                v = ld_acquire_u64(cell);
+                if ((uint32_t)v == pos + 1u) break;
                 if ((++spins & 7) == 0) {
                     if (stopped(P)) { quit = 1; break; }
                     const unsigned long long now = globaltimer_ns();
@@ -1133,9 +1166,11 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             unsigned long long tw = 0;
             while (true) {
                 bool ok = true;
-                if (w0) ok = (int32_t)(ld_relaxed_u32(&done[lane]) - i0) >= 0;
-                if (w1) ok = ok && (int32_t)(ld_relaxed_u32(&done[lane + 32]) - i1) >= 0;
-                if (__all_sync(0xffffffffu, ok)) { fence_acq_rel_gpu(); break; }
+                // acquire loads of the done words (released by the upstream
+                // tasks' last CTAs); the barrier below passes them to the CTA
+                if (w0) ok = (int32_t)(ld_acquire_u32(&done[lane]) - i0) >= 0;
+                if (w1) ok = ok && (int32_t)(ld_acquire_u32(&done[lane + 32]) - i1) >= 0;
+                if (__all_sync(0xffffffffu, ok)) break;
                 if ((++spins & 7) == 0) {
                     const bool stop = stopped(P);
                     const unsigned long long now = globaltimer_ns();

@@ -152,6 +152,21 @@ def test_free_slot_variant(W, M):
     assert max(active) <= W - 1
 
 
+def test_trace_timestamps_follow_each_task_through_its_states():
+    """Per task: insertion <= publication <= first-CTA start <= last-CTA end
+    <= retirement seen, on one device clock."""
+    s = sg.elementwise_stream(17, n_tasks=300, ranges=True)
+    bufs = harness.DeviceBuffers(s.buffers)
+    with harness.Context(8, trace=True) as ctx:
+        ids, packed = harness.pack_tasks(s.tasks, bufs)
+        ctx.submit_packed(ids, packed)
+        ctx.flush()
+        ctx.sync()
+        tr = ctx.trace(0, 0, len(ids)).astype(np.int64)
+    assert (tr > 0).all()
+    assert (np.diff(tr, axis=1) >= 0).all()
+
+
 def test_free_slot_rlsim_emission():
     p = sg.RLParams(n_env=64, steps=5)
     sim = sg.RLSim(6, p)
