@@ -197,8 +197,10 @@ struct KParams {
     unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
                               // (descriptor index << 8 | CTA index)
     TaskAux *taskaux;         // [n_streams][capacity], like recs
-    uint32_t *done;           // [n_streams][kMaxWindow]: seq + 1 of the slot's retired task
-    uint32_t *remaining;      // [n_streams][kMaxWindow]: CTAs of the slot's task that finished
+    // [n_streams][kMaxWindow] done words: (seq + 1) << 32 | CTAs not yet
+    // finished, of the slot's latest task (set when it is published; each CTA
+    // subtracts one with release semantics)
+    unsigned long long *done;
     unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
     SchedStats *sched_stats;  // [n_streams]
     unsigned long long *trace;  // [n_streams][log_capacity][kTraceFields] (ACS_FLAG_TRACE)
@@ -243,7 +245,7 @@ struct PubQueue {
 
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    const uint32_t base = H * 336u + H * 8 + H * 4 + 16 + 8 + kMaxWindow * 4;
+    const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + 8 + kMaxWindow * 4 * 2;
     return (base + 15u) / 16u * 16u + (uint32_t)sizeof(PubQueue);
 }
 

@@ -62,6 +62,16 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     return v;
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// A done word shows task `want - 1` (want = seq + 1) complete when it names
+// that task with no CTA left, or names a later task of the slot (which the
+// slot takes only after the earlier one retired).
+__device__ __forceinline__ bool slot_done(unsigned long long w, uint32_t want) {
+    const uint32_t hi = (uint32_t)(w >> 32);
+    return (int32_t)(hi - want) > 0 || (hi == want && (uint32_t)w == 0u);
+}
 // system scope: words in mapped host memory (resident launches)
 __device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
     uint32_t v;
@@ -126,11 +136,16 @@ struct SchedShared {
     uint32_t next;           // tasks below are inserted
     uint32_t quit;           // 1: checkers and loader leave
     uint32_t end;            // stream end known to the CTA (grows while the stream is open)
+    uint32_t head_pos;       // sole producer: work-ring position of the oldest unreleased task's
+                             // first unit (every unit below it belongs to a retired task)
+    uint32_t pad[3];
 };
+static_assert(sizeof(SchedShared) == 32, "SchedShared size (sched_smem_bytes)");
 
 struct SchedSmem {
     unsigned long long *retired;  // slots the poller saw retire, not yet taken by warp 0
     uint32_t *expect;        // [kMaxWindow] done value of each executing slot (0: none)
+    uint32_t *slotpos;       // [kMaxWindow] sole producer: first work-ring position of the slot's task
     HistRec *hist;
     unsigned long long *pmask;
     uint32_t *ptag;
@@ -154,6 +169,8 @@ __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     s.retired = reinterpret_cast<unsigned long long *>(p);
     p += sizeof(unsigned long long);
     s.expect = reinterpret_cast<uint32_t *>(p);
+    p += kMaxWindow * sizeof(uint32_t);
+    s.slotpos = reinterpret_cast<uint32_t *>(p);
     p += kMaxWindow * sizeof(uint32_t);
     p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15u) & ~(uintptr_t)15u);
     s.pub = reinterpret_cast<PubQueue *>(p);
@@ -374,7 +391,7 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     SchedSmem S = carve(smem_raw, W);
-    const uint32_t *done = P.done + stream * kMaxWindow;
+    const unsigned long long *done = P.done + stream * kMaxWindow;
     uint32_t backoff = 32;
     while (!lds_volatile(&S.sh->quit)) {
         const uint32_t e0 = lane < W ? lds_volatile(&S.expect[lane]) : 0u;
@@ -382,8 +399,8 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
         bool h0 = false, h1 = false;
         // acquire loads: a done word read at its task's value orders the
         // task's writes before what this lane does next
-        if (e0) h0 = (int32_t)(ld_acquire_u32(&done[lane]) - e0) >= 0;
-        if (e1) h1 = (int32_t)(ld_acquire_u32(&done[lane + 32]) - e1) >= 0;
+        if (e0) h0 = slot_done(ld_acquire_u64(&done[lane]), e0);
+        if (e1) h1 = slot_done(ld_acquire_u64(&done[lane + 32]), e1);
         const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
         if (b0 | b1) {
             __syncwarp();                        // ... and, among the lanes, before lane 0 posts
@@ -501,6 +518,7 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->next = first;
         S.sh->quit = 0;
         S.sh->end = P.end[stream];
+        S.sh->head_pos = 0;
         if (P.open[stream] || P.resident) {   // published before any emitter of this launch can run
             StreamCtl *sc = &P.sctl[stream];
             sc->end = P.end[stream];
@@ -527,12 +545,7 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const bool sole_producer = P.n_streams == 1;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     uint32_t done_b = 0, backoff = 32;
-    // sole producer: batches fill consecutive positions; after each pass the
-    // sequence words of the kPreCells cells from pre_base on are read (lane l
-    // holds base + l + 32 k in pre[k]) for the checks of the next pass
-    constexpr uint32_t kPreCells = 128;
-    uint32_t pre_base = 0, pre0 = 0, pre1 = 0, pre2 = 0, pre3 = 0;
-    bool have_pre = false;
+    const uint32_t ncells = P.cell_mask + 1u;
     while (true) {
         const uint32_t prod = lds_volatile(&S.pub->produced);
         if (prod == done_b) {
@@ -543,17 +556,12 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         }
         backoff = 32;
         __threadfence_block();
-        // free cells among the prefetched ones, one bit per position
-        uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0;
-        if (have_pre) {
-            f0 = __ballot_sync(0xffffffffu, pre0 == pre_base + lane);
-            f1 = __ballot_sync(0xffffffffu, pre1 == pre_base + 32u + lane);
-            f2 = __ballot_sync(0xffffffffu, pre2 == pre_base + 64u + lane);
-            f3 = __ballot_sync(0xffffffffu, pre3 == pre_base + 96u + lane);
-        }
+        // sole producer: a cell whose previous unit lies below head_pos was
+        // read by its worker before that unit's task retired (the fence below
+        // orders this read of head_pos before the cells are written)
+        const uint32_t head_pos = sole_producer ? lds_volatile(&S.sh->head_pos) : 0u;
         // 1. every pending batch: aux words, then its cells checked free
         bool ok = true;
-        uint32_t last_end = 0;
         for (uint32_t b = done_b; b != prod && ok; ++b) {
             const PubBatch &B = S.pub->b[b % kPubSlots];
             const uint32_t nins = B.nins, p0 = B.p0, total = B.total;
@@ -562,14 +570,14 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                 const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
                 const unsigned long long up = B.up[lane];
                 *reinterpret_cast<uint4 *>(&P.taskaux[gidx]) = make_uint4((uint32_t)up, (uint32_t)(up >> 32), q, 0u);
+                // the slot's done word names the task with all its CTAs to go
+                // (its previous task retired; waiters may still read the word)
+                st_relaxed_u64(&P.done[stream * kMaxWindow + q % P.window],
+                               ((unsigned long long)(q + 1u) << 32) | B.n[lane]);
             }
-            last_end = p0 + total;
             for (uint32_t u = lane; u < total && ok; u += 32) {
-                const uint32_t x = p0 + u, d = x - pre_base;
-                if (have_pre && d < kPreCells) {
-                    const uint32_t f = d < 32 ? f0 : d < 64 ? f1 : d < 96 ? f2 : f3;
-                    if ((f >> (d & 31)) & 1u) continue;
-                }
+                const uint32_t x = p0 + u;
+                if (sole_producer && (int32_t)(x - ncells - head_pos) < 0) continue;
                 unsigned long long *cell = &P.cells[x & P.cell_mask];
                 unsigned long long tw = 0;
                 uint32_t spins = 0;
@@ -611,15 +619,6 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         done_b = prod;
         __syncwarp();
         if (lane == 0) sts_volatile(&S.pub->consumed, done_b);
-        // the cells the following batches start on (sole producer)
-        if (sole_producer) {
-            pre_base = last_end;
-            pre0 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + lane) & P.cell_mask]);
-            pre1 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 32u + lane) & P.cell_mask]);
-            pre2 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 64u + lane) & P.cell_mask]);
-            pre3 = (uint32_t)ld_relaxed_u64(&P.cells[(pre_base + 96u + lane) & P.cell_mask]);
-            have_pre = true;
-        }
     }
 }
 
@@ -646,6 +645,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     uint32_t hslot = first % W, nslot = first % W;   // head % W, next % W
     const bool sole_producer = P.n_streams == 1;
     uint32_t tail = sole_producer ? ld_volatile_u32(&P.ctl->ring_tail) : 0u;
+    if (sole_producer && lane == 0) sts_volatile(&S.sh->head_pos, tail);   // earlier launches' units are consumed
     uint32_t pub_prod = 0;                          // batches handed to the publisher
     unsigned long long idle_since = 0;
     uint32_t iter = 0;
@@ -693,6 +693,13 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             head += run;
             hslot += run;
             if (hslot >= W) hslot -= W;
+            if (sole_producer && run) {
+                // every unit below the first one of the oldest unreleased task
+                // belongs to a retired task, so its worker has read it
+                const uint32_t hp = head == next ? tail : S.slotpos[hslot];
+                __threadfence_block();   // after the retirements taken above
+                if (lane == 0) sts_volatile(&S.sh->head_pos, hp);
+            }
         }
         ACS_PHASE(2);
         // 2. how many tasks are checked and have a free slot (at most 32 per
@@ -761,6 +768,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             my_off = incl - my_n;
             if (mine) {
                 my_up = up;
+                S.slotpos[js] = p0 + my_off;
                 if (logging || tracing) {
                     const size_t li = lbase + (q & LM);
                     if (logging) {
@@ -772,6 +780,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                         const unsigned long long now = globaltimer_ns();
                         P.trace[li * kTraceFields + 0] = now;   // field 1: the publisher warp
                         P.trace[li * kTraceFields + 2] = ~0ull;   // first-CTA start: atomicMin target
+                        P.trace[li * kTraceFields + 3] = 0ull;    // last-CTA end: atomicMax target
                     }
                 }
             }
@@ -1158,7 +1167,7 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         // task in slot b is seq - ((seq - b) mod W); done words only grow
         const unsigned long long up = s_up;
         if (up && threadIdx.x < 32) {
-            const uint32_t *done = P.done + stream * kMaxWindow;
+            const unsigned long long *done = P.done + stream * kMaxWindow;
             const bool w0 = (up >> lane) & 1ull, w1 = lane + 32 < W && ((up >> (lane + 32)) & 1ull);
             const uint32_t i0 = seq - ((seq - lane + 64u * W) % W) + 1u;
             const uint32_t i1 = seq - ((seq - lane - 32u + 64u * W) % W) + 1u;
@@ -1168,8 +1177,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                 bool ok = true;
                 // acquire loads of the done words (released by the upstream
                 // tasks' last CTAs); the barrier below passes them to the CTA
-                if (w0) ok = (int32_t)(ld_acquire_u32(&done[lane]) - i0) >= 0;
-                if (w1) ok = ok && (int32_t)(ld_acquire_u32(&done[lane + 32]) - i1) >= 0;
+                if (w0) ok = slot_done(ld_acquire_u64(&done[lane]), i0);
+                if (w1) ok = ok && slot_done(ld_acquire_u64(&done[lane + 32]), i1);
                 if (__all_sync(0xffffffffu, ok)) break;
                 if ((++spins & 7) == 0) {
                     const bool stop = stopped(P);
@@ -1200,25 +1209,14 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         else run_body(s_hdr, (int)cta, smem, &P.ctl->stop);
         __syncthreads();
         if (threadIdx.x == 0) {
-            bool last = true;
-            if (s_hdr.ncta > 1) {
-                // CTAs of one task count themselves; the last one resets the
-                // counter for the slot's next task and publishes completion
-                __threadfence();
-                uint32_t *cnt = &P.remaining[stream * kMaxWindow + slot];
-                last = atomicAdd(cnt, 1u) + 1u == (uint32_t)s_hdr.ncta;
-                if (last) st_relaxed_u32(cnt, 0u);
-            }
-            if (last) {
-                if (tracing)
-                    P.trace[(((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))) * kTraceFields + 3] =
-                        globaltimer_ns();
-                if (logging) {
-                    const unsigned long long t = atomicAdd(&P.ctl->ticket, 1ull);
-                    P.log_retire[((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u))] = t;
-                }
-                st_release_u32(&P.done[stream * kMaxWindow + slot], seq + 1u);
-            }
+            // every CTA stamps its end (the task's is the latest) and then
+            // takes itself off the done word's CTA count with release
+            // semantics: the CTA that reaches zero completes the task, with
+            // no round trip and no reset for the slot's next task
+            const size_t li = ((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u));
+            if (tracing) atomicMax(&P.trace[li * kTraceFields + 3], globaltimer_ns());
+            if (logging) atomicMax(&P.log_retire[li], atomicAdd(&P.ctl->ticket, 1ull));
+            red_release_add_u64(&P.done[stream * kMaxWindow + slot], ~0ull);   // - 1 in the low half
         }
     }
 }
@@ -1259,11 +1257,11 @@ __global__ void __launch_bounds__(kBlock, 2) acs_persistent_kernel(const __grid_
     }
 }
 
-__global__ void acs_init_kernel(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, uint32_t *done,
-                                uint32_t *remaining, uint32_t nslots) {
+__global__ void acs_init_kernel(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, unsigned long long *done,
+                                uint32_t nslots) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t q = i; q < ncells; q += gridDim.x * blockDim.x) cells[q] = q;
-    for (uint32_t q = i; q < nslots; q += gridDim.x * blockDim.x) { done[q] = 0; remaining[q] = 0; }
+    for (uint32_t q = i; q < nslots; q += gridDim.x * blockDim.x) done[q] = 0;
     if (i == 0) {
         ctl->ring_head = 0; ctl->ring_tail = 0; ctl->stop = 0; ctl->sched_done = 0;
         ctl->exit_count = 0; ctl->err = 0; ctl->err_info = 0; ctl->ticket = 0;
@@ -1283,9 +1281,9 @@ __global__ void __launch_bounds__(kBlock) acs_body_kernel(const __grid_constant_
 namespace acs {
 const void *persistent_kernel_fn() { return (const void *)acs_persistent_kernel; }
 const void *body_kernel_fn() { return (const void *)acs_body_kernel; }
-cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, uint32_t *done, uint32_t *remaining,
+cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, unsigned long long *done,
                         uint32_t nslots, cudaStream_t st) {
-    acs_init_kernel<<<148, 256, 0, st>>>(cells, ncells, ctl, done, remaining, nslots);
+    acs_init_kernel<<<148, 256, 0, st>>>(cells, ncells, ctl, done, nslots);
     return cudaGetLastError();
 }
 }  // namespace acs

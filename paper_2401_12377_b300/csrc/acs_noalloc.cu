@@ -25,7 +25,7 @@
 
 namespace acs {
 const void *persistent_kernel_fn();
-cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, uint32_t *done, uint32_t *remaining,
+cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, unsigned long long *done,
                         uint32_t nslots, cudaStream_t st);
 }  // namespace acs
 
@@ -45,8 +45,7 @@ constexpr size_t kOffCells = kOffRing + up(sizeof(TaskRec) * ACS_NOALLOC_MAX_TAS
 constexpr size_t kOffAux = kOffCells + up(sizeof(unsigned long long) * kNoAllocCells);
 constexpr size_t kOffCtl = kOffAux + up(sizeof(TaskAux) * ACS_NOALLOC_MAX_TASKS);
 constexpr size_t kOffDone = kOffCtl + up(sizeof(DevCtl));
-constexpr size_t kOffRemaining = kOffDone + up(sizeof(uint32_t) * kMaxWindow);
-constexpr size_t kOffLog = kOffRemaining + up(sizeof(uint32_t) * kMaxWindow);      // 3 x 1 entry
+constexpr size_t kOffLog = kOffDone + up(sizeof(unsigned long long) * kMaxWindow);   // 3 x 1 entry
 constexpr size_t kOffTrace = kOffLog + up(3 * sizeof(unsigned long long));
 constexpr size_t kOffStats = kOffTrace + up(kTraceFields * sizeof(unsigned long long));
 constexpr size_t kOffStatus = kOffStats + up(sizeof(SchedStats));
@@ -154,15 +153,14 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     unsigned long long *cells = reinterpret_cast<unsigned long long *>(base + kOffCells);
     TaskAux *aux = reinterpret_cast<TaskAux *>(base + kOffAux);
     DevCtl *ctl = reinterpret_cast<DevCtl *>(base + kOffCtl);
-    uint32_t *done = reinterpret_cast<uint32_t *>(base + kOffDone);
-    uint32_t *remaining = reinterpret_cast<uint32_t *>(base + kOffRemaining);
+    unsigned long long *done = reinterpret_cast<unsigned long long *>(base + kOffDone);
     unsigned long long *logs = reinterpret_cast<unsigned long long *>(base + kOffLog);
     unsigned long long *trace = reinterpret_cast<unsigned long long *>(base + kOffTrace);
     SchedStats *stats = reinterpret_cast<SchedStats *>(base + kOffStats);
     HostStatus *status = reinterpret_cast<HostStatus *>(base + kOffStatus);
 
     // what must start from zero: ring cells, counters, done words, status
-    if (launch_init(cells, kNoAllocCells, ctl, done, remaining, kMaxWindow, st) != cudaSuccess) return ACS_ERR_DEVICE;
+    if (launch_init(cells, kNoAllocCells, ctl, done, kMaxWindow, st) != cudaSuccess) return ACS_ERR_DEVICE;
     if (cudaMemsetAsync(stats, 0, sizeof(SchedStats), st) != cudaSuccess ||
         cudaMemsetAsync(status, 0, sizeof(HostStatus), st) != cudaSuccess ||
         cudaMemcpyAsync(ring, g_stage, (size_t)n * sizeof(TaskRec), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -175,7 +173,6 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     P.cells = cells;
     P.taskaux = aux;
     P.done = done;
-    P.remaining = remaining;
     P.log_mask = logs;
     P.log_start = logs + 1;
     P.log_retire = logs + 2;

@@ -25,7 +25,7 @@
 namespace acs {
 const void *persistent_kernel_fn();
 const void *body_kernel_fn();
-cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, uint32_t *done, uint32_t *remaining,
+cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl, unsigned long long *done,
                         uint32_t nslots, cudaStream_t st);
 }  // namespace acs
 
@@ -97,7 +97,7 @@ struct acs_ctx {
     TaskRec *h_ring = nullptr;  // pinned [S][C]
     TaskRec *d_ring = nullptr;
     DevCtl *d_ctl = nullptr;
-    uint32_t *d_done = nullptr, *d_remaining = nullptr;
+    unsigned long long *d_done = nullptr;
     unsigned long long *d_cells = nullptr;
     TaskAux *d_taskaux = nullptr;
     uint32_t ncells = 0;
@@ -234,7 +234,6 @@ void fill_params(acs_ctx *c, KParams &P) {
     P.cells = c->d_cells;
     P.taskaux = c->d_taskaux;
     P.done = c->d_done;
-    P.remaining = c->d_remaining;
     P.log_mask = c->d_log_mask;
     P.log_start = c->d_log_start;
     P.log_retire = c->d_log_retire;
@@ -669,7 +668,6 @@ void acs_destroy(acs_ctx *c) {
     cudaFree(c->d_ring);
     cudaFree(c->d_ctl);
     cudaFree(c->d_done);
-    cudaFree(c->d_remaining);
     cudaFree(c->d_cells);
     cudaFree(c->d_taskaux);
     cudaFree(c->d_log_mask);
@@ -748,8 +746,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMalloc(&c->d_ring, nrec * sizeof(TaskRec)));
     chk(cudaMalloc(&c->d_ctl, sizeof(DevCtl)));
     const uint32_t nslots = c->S * kMaxWindow;
-    chk(cudaMalloc(&c->d_done, nslots * sizeof(uint32_t)));
-    chk(cudaMalloc(&c->d_remaining, nslots * sizeof(uint32_t)));
+    chk(cudaMalloc(&c->d_done, nslots * sizeof(unsigned long long)));
     // work ring: at most (2W - 1) * ACS_MAX_NCTA units of one stream are in flight
     uint32_t cells = 1;
     while (cells < std::min<uint32_t>(2u * c->W * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;
@@ -778,7 +775,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaMemsetAsync(c->d_sched_stats, 0, c->S * sizeof(SchedStats), c->stream));
     chk(cudaMemsetAsync(c->d_sctl, 0, c->S * sizeof(StreamCtl), c->stream));
     chk(cudaMemsetAsync(c->d_log_mask, 0, nlog * sizeof(unsigned long long), c->stream));
-    chk(launch_init(c->d_cells, c->ncells, c->d_ctl, c->d_done, c->d_remaining, nslots, c->stream));
+    chk(launch_init(c->d_cells, c->ncells, c->d_ctl, c->d_done, nslots, c->stream));
 
     // grid: one scheduler CTA per stream + worker CTAs, all co-resident
     c->smem = dyn_smem_bytes(c->W);
