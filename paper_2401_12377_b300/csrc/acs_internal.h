@@ -245,7 +245,7 @@ struct PubQueue {
 
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + 8 + kMaxWindow * 4 * 2;
+    const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + kMaxWindow * 4 * 2;
     return (base + 15u) / 16u * 16u + (uint32_t)sizeof(PubQueue);
 }
 

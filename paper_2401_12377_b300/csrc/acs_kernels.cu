@@ -114,7 +114,6 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 //               each conflicting predecessor i in [seq - W + 1, seq - 1])
 //   ptag[H]     seq + 1 once pmask of seq is written (0: not yet)
 //   sh          counters shared by the warps
-//   retired     slots the poller saw retire, not yet taken by warp 0
 //   expect[64]  the done value each executing slot waits for (0: none)
 //   pub         the insertion batches handed from warp 0 to the publisher
 //
@@ -143,7 +142,6 @@ struct SchedShared {
 static_assert(sizeof(SchedShared) == 32, "SchedShared size (sched_smem_bytes)");
 
 struct SchedSmem {
-    unsigned long long *retired;  // slots the poller saw retire, not yet taken by warp 0
     uint32_t *expect;        // [kMaxWindow] done value of each executing slot (0: none)
     uint32_t *slotpos;       // [kMaxWindow] sole producer: first work-ring position of the slot's task
     HistRec *hist;
@@ -166,8 +164,6 @@ __device__ __forceinline__ SchedSmem carve(uint8_t *smem, uint32_t W) {
     p += s.H * sizeof(uint32_t);
     s.sh = reinterpret_cast<SchedShared *>(p);
     p += sizeof(SchedShared);
-    s.retired = reinterpret_cast<unsigned long long *>(p);
-    p += sizeof(unsigned long long);
     s.expect = reinterpret_cast<uint32_t *>(p);
     p += kMaxWindow * sizeof(uint32_t);
     s.slotpos = reinterpret_cast<uint32_t *>(p);
@@ -200,23 +196,41 @@ __device__ __forceinline__ NewTask load_new_task(const TaskRec &rj) {
     return t;
 }
 
-__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const NewTask &t, const TaskRec &rj) {
-    const int ni = min((int)ri.nseg, kMaxSegs);
-    const uint32_t wi = ri.wmask;
-    bool hit = false;
+// Every segment pair of a candidate (ri) and the new task (t, all segments
+// also in rj), from shared memory: tasks with more than kRegSegs segments.
+__device__ __noinline__ bool rec_conflict_all(const TaskRec &ri, const TaskRec &rj) {
+    const int ni = min((int)ri.nseg, kMaxSegs), nj = min((int)rj.nseg, kMaxSegs);
+    const uint32_t wi = ri.wmask, wj = rj.wmask;
     for (int y = 0; y < ni; ++y) {
         const Seg b = ri.seg[y];
         const bool yw = (wi >> y) & 1u;
-#pragma unroll
-        for (int x = 0; x < kRegSegs; ++x)
-            hit |= x < (int)t.n && (yw || ((t.w >> x) & 1u)) && t.a[x].start <= b.last && b.start <= t.a[x].last;
-        for (uint32_t x = kRegSegs; x < t.n; ++x) {
+        for (int x = 0; x < nj; ++x) {
             const Seg a = rj.seg[x];
-            hit |= (yw || ((t.w >> x) & 1u)) && a.start <= b.last && b.start <= a.last;
+            if ((yw || ((wj >> x) & 1u)) && a.start <= b.last && b.start <= a.last) return true;
         }
-        if (hit) return true;
     }
     return false;
+}
+
+// The candidate's first kRegSegs segments are loaded together and every pair
+// with the new task's registers is tested (predicated, no early exit).
+__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const NewTask &t, const TaskRec &rj) {
+    const uint32_t ni = min((uint32_t)ri.nseg, (uint32_t)kMaxSegs);
+    const uint32_t wi = ri.wmask;
+    Seg b[kRegSegs];
+#pragma unroll
+    for (int y = 0; y < kRegSegs; ++y) b[y] = ri.seg[y];    // unused entries are masked below
+    bool hit = false;
+#pragma unroll
+    for (int y = 0; y < kRegSegs; ++y) {
+        const bool yv = (uint32_t)y < ni, yw = (wi >> y) & 1u;
+#pragma unroll
+        for (int x = 0; x < kRegSegs; ++x)
+            hit |= yv && (uint32_t)x < t.n && (yw || ((t.w >> x) & 1u)) && t.a[x].start <= b[y].last &&
+                   b[y].start <= t.a[x].last;
+    }
+    if (!hit && (ni > (uint32_t)kRegSegs || t.n > (uint32_t)kRegSegs)) hit = rec_conflict_all(ri, rj);
+    return hit;
 }
 
 // Warp 7: copies descriptors from the stream's device ring into hist with
@@ -383,10 +397,10 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
 }
 
 // Warp 6: polls the done word of every executing slot (acquire loads) and
-// posts the slots whose task retired into a shared bitmask; those acquires,
-// with the publisher's fence before it publishes work, order the retired
-// tasks' writes before every dependent's start. Warp 0 never waits on global
-// memory to retire tasks.
+// clears the slot's expect word once its task completed; those acquires, with
+// the publisher's fence before it publishes work, order the retired tasks'
+// writes before every dependent's start. Warp 0 never waits on global memory
+// to retire tasks.
 __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
@@ -403,12 +417,10 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
         if (e1) h1 = slot_done(ld_acquire_u64(&done[lane + 32]), e1);
         const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
         if (b0 | b1) {
-            __syncwarp();                        // ... and, among the lanes, before lane 0 posts
+            // release at CTA scope: warp 0 retires a slot once it reads 0 here
+            __threadfence_block();
             if (h0) sts_volatile(&S.expect[lane], 0u);
             if (h1) sts_volatile(&S.expect[lane + 32], 0u);
-            __threadfence_block();
-            if (lane == 0) atomicOr(S.retired, (unsigned long long)b0 | ((unsigned long long)b1 << 32));
-            __syncwarp();
             backoff = 32;
         } else {
             const bool any = __any_sync(0xffffffffu, e0 | e1);
@@ -440,7 +452,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             const uint32_t nx = lds_volatile(&S.sh->next);
             if (cu > j && j < nx + H) break;
             if (lds_volatile(&S.sh->quit)) {
-                if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
+                if (seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
                 if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
                 return;
             }
@@ -457,12 +469,14 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             __nanosleep(backoff);
             if (backoff < 256) backoff <<= 1;
         }
-        if (lane == 0) {   // algorithmic bytes: what the task's segments name
+        {   // algorithmic bytes: what the task's segments name (lane k: segment k)
             const TaskRec &rr = S.hist[j & HM].r;
-            for (uint32_t k = 0; k < rr.nseg && k < (uint32_t)kMaxSegs; ++k)
-                if (!(rr.seg[k].start == 0 && rr.seg[k].last == ~0ull))
-                    seg_bytes += (rr.seg[k].last - rr.seg[k].start + 1) *
-                                 (1u + (k < 8 ? ((rr.wmask >> k) & (rr.flags >> k) & 1u) : 0u));
+            if (lane < min((uint32_t)rr.nseg, (uint32_t)kMaxSegs)) {
+                const Seg g = rr.seg[lane];
+                if (!(g.start == 0 && g.last == ~0ull))
+                    seg_bytes += (g.last - g.start + 1) *
+                                 (1u + (lane < 8 ? ((rr.wmask >> lane) & (rr.flags >> lane) & 1u) : 0u));
+            }
         }
         tw = 0;
         __threadfence_block();
@@ -477,28 +491,29 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         const NewTask nt = load_new_task(rj);
         if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM].r, nt, rj);
         if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM].r, nt, rj);
-        const uint32_t b0 = __ballot_sync(0xffffffffu, c0);
-        const uint32_t b1 = __ballot_sync(0xffffffffu, c1);
+        // candidate at distance d sits in slot (j - d) mod W; each lane sets
+        // the bits of its conflicting candidates, two OR reductions merge them
+        const uint32_t js = j % W;
+        uint32_t mlo = 0, mhi = 0;
+        if (c0) {
+            const uint32_t sl = js >= d0 ? js - d0 : js + W - d0;
+            if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
+        }
+        if (c1) {
+            const uint32_t sl = js >= d1 ? js - d1 : js + W - d1;
+            if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
+        }
+        mlo = __reduce_or_sync(0xffffffffu, mlo);
+        mhi = __reduce_or_sync(0xffffffffu, mhi);
         if (lane == 0) {
-            // candidate at distance d sits in slot (j - d) mod W
-            const uint32_t js = j % W;
-            unsigned long long m = 0;
-            for (uint32_t bits = b0; bits; bits &= bits - 1) {
-                const uint32_t d = (uint32_t)__ffs(bits);          // 1 .. 32
-                m |= 1ull << (js >= d ? js - d : js + W - d);
-            }
-            for (uint32_t bits = b1; bits; bits &= bits - 1) {
-                const uint32_t d = (uint32_t)__ffs(bits) + 32u;    // 33 .. 63
-                m |= 1ull << (js >= d ? js - d : js + W - d);
-            }
-            S.pmask[j & HM] = m;
+            S.pmask[j & HM] = (unsigned long long)mlo | ((unsigned long long)mhi << 32);
             __threadfence_block();
             sts_volatile(&S.ptag[j & HM], j + 1u);
             if (tracing) check_cycles += clock64() - tc0;
         }
         __syncwarp();
     }
-    if (lane == 0 && seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
+    if (seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
     if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
 }
 
@@ -511,7 +526,6 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     for (uint32_t i = threadIdx.x; i < S.H; i += blockDim.x) S.ptag[i] = 0;
     for (uint32_t i = threadIdx.x; i < (uint32_t)kMaxWindow; i += blockDim.x) S.expect[i] = 0;
     if (threadIdx.x == 0) {
-        *S.retired = 0ull;
         S.pub->produced = 0;
         S.pub->consumed = 0;
         S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
@@ -668,14 +682,14 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         ACS_PHASE(0);
         const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
         // 1. retire the slots the poller warp saw complete, first, so that a
-        //    slot released now takes a task in this same iteration
-        unsigned long long R = 0;
-        if (lane == 0) R = atomicExch(S.retired, 0ull);
-        R = ((unsigned long long)__shfl_sync(0xffffffffu, (uint32_t)(R >> 32), 0) << 32) |
-            __shfl_sync(0xffffffffu, (uint32_t)R, 0);
-        const bool ret0 = (R >> lane) & 1ull;
-        const bool ret1 = W > 32 && ((R >> (lane + 32)) & 1ull);
-        if (R) {
+        //    slot released now takes a task in this same iteration: an
+        //    executing slot whose expect word the poller cleared (each lane
+        //    reads the words of its own two slots)
+        const bool ret0 = st0 == kExec && lds_volatile(&S.expect[lane]) == 0u;
+        const bool ret1 = W > 32 && st1 == kExec && lds_volatile(&S.expect[lane + 32]) == 0u;
+        if (__any_sync(0xffffffffu, ret0 || ret1)) {
+            __threadfence_block();   // acquire: what the poller acquired before clearing ...
+            __syncwarp();            // ... for every lane of the warp
             progress = true;
             if (ret0) st0 = kRetired;
             if (ret1) st1 = kRetired;
@@ -747,13 +761,17 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             const unsigned long long low = (1ull << lane) - 1ull;
             const unsigned long long newer = nslot ? (((low << nslot) | (low >> (W - nslot))) & full) : low;
             const unsigned long long up = pre & (act | newer);
-            uint32_t incl = my_n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += v;
+            // exclusive prefix sum of the CTA counts, one ballot per bit plane
+            // (independent of each other, unlike a shuffle scan)
+            const uint32_t planes = 32u - (uint32_t)__clz(__reduce_or_sync(0xffffffffu, my_n));
+            const uint32_t below = (1u << lane) - 1u;
+            uint32_t excl = 0;
+            total = 0;
+            for (uint32_t b = 0; b < planes; ++b) {
+                const uint32_t m = __ballot_sync(0xffffffffu, (my_n >> b) & 1u);
+                excl += (uint32_t)__popc(m & below) << b;
+                total += (uint32_t)__popc(m) << b;
             }
-            total = __shfl_sync(0xffffffffu, incl, 31);
             if (sole_producer) {
                 p0 = tail;
             } else {
@@ -765,7 +783,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             ACS_PHASE(3);
             ACS_PHASE(4);
             js = nslot + lane >= W ? nslot + lane - W : nslot + lane;
-            my_off = incl - my_n;
+            my_off = excl;
             if (mine) {
                 my_up = up;
                 S.slotpos[js] = p0 + my_off;
@@ -806,7 +824,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         // 4. hand this iteration's insertion batch to the publisher warp (its
         //    fence then orders the log entries above and the retirements seen
         //    through the poller before the new units: conflicts farther back
-        //    than W - 1 rely on that alone)
+        //    than W - 1 rely on that alone); a slot's expect word is set here,
+        //    after its task is marked executing, and read again only in a
+        //    later iteration
         if (nins) {
             uint32_t spins = 0;
             unsigned long long tw = 0;
@@ -914,7 +934,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
                 break;
             }
         }
-        if (((++iter & 31) == 0 || !progress) && stopped(P)) { failed = true; break; }
+        if ((++iter & 31) == 0 && stopped(P)) { failed = true; break; }
     }
     (void)failed;
     if (sole_producer && lane == 0) st_relaxed_u32(&P.ctl->ring_tail, tail);
