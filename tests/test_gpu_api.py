@@ -159,3 +159,31 @@ def test_independent_streams_in_one_launch():
             out = bufs[i].download()
             assert all(np.array_equal(out[k], ref[k]) for k in ref)
         assert ctx.stats()["launches"] == 1
+
+
+@pytest.mark.parametrize("W", [8, 32, 64])
+def test_tasks_with_many_segments(W):
+    """NOP tasks with 1 to 16 segments each over a small address range, so
+    that many pairs conflict: tasks with up to 4 segments on both sides take
+    the checker's register path, the others its all-pairs path. Logged masks
+    equal the oracle's D_W and the start/retire log is legal against E."""
+    rng = np.random.default_rng(1234 + W)
+    base = 1 << 20
+    segs = []
+    for _ in range(300):
+        nr = int(rng.integers(0, 9))
+        nw = int(rng.integers(0 if nr else 1, 9))
+        def one():
+            size = int(rng.integers(0, 513)) if rng.random() < 0.95 else 0
+            return (base + int(rng.integers(0, 1 << 16)), size)
+        segs.append(([one() for _ in range(nr)], [one() for _ in range(nw)]))
+    with harness.Context(W, log=True) as ctx:
+        for tid, (rd, wr) in enumerate(segs):
+            assert acs.acs_submit(ctx.h, tid, _nop_args(1 + tid % 3), rd, wr) == acs.ACS_OK
+        ctx.flush()
+        ctx.sync()
+        masks, start, retire = ctx.log(0, 0, len(segs))
+    E = deps.full_dag(segs)
+    assert deps.edges_from_masks([int(m) for m in masks], W) == deps.window_dag(E, W)
+    assert not deps.check_legal(E, [int(x) for x in start], [int(x) for x in retire])
+    assert sum(1 for rd, wr in segs if len(rd) + len(wr) > 4) > 100
