@@ -62,6 +62,11 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     return v;
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// Bulk prefetch of [p, p + bytes) into L2 (a hint: no data moves to the SM);
+// p and bytes multiples of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -1182,6 +1187,18 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         if (gidx >= nrec) {   // self-check: payload names a ring entry
             if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerPayload);
             continue;
+        }
+        // a GEMV unit's weight rows depend on no task: start moving them into L2
+        // now, while the unit may still wait for its upstream tasks
+        if (threadIdx.x == 0 && s_hdr.op == ACS_OP_GEMV && cta < s_hdr.ncta) {
+            const acs_gemv_args g = load_args<acs_gemv_args>(s_hdr.args);
+            const uint32_t rpc = (g.m + s_hdr.ncta - 1) / s_hdr.ncta;
+            const uint32_t r0 = min(g.m, rpc * cta), r1 = min(g.m, r0 + rpc);
+            const uint64_t a = g.W + (uint64_t)r0 * g.k * 4u, bytes = (uint64_t)(r1 - r0) * g.k * 4u;
+            if (((a | bytes) & 15u) == 0)
+                for (uint64_t o = 0; o < bytes; o += 32768u)
+                    prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
+                                     (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
         // wait until every upstream task still active at dispatch retired: the
         // task in slot b is seq - ((seq - b) mod W); done words only grow
