@@ -81,7 +81,7 @@ def parse():
 # kernel's sources hash to the value it was taken with (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3639552, "sources_sha1": "c796914d2faffbaa2d2deeff6a17e94765f89061"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3639552, "sources_sha1": "c52ed274a495cc17a86afb0cb3554b364afabc86"}
 
 
 def kernel_sources_sha1() -> str:

@@ -18,8 +18,8 @@
 //          use (and, in a resident launch, follows the host-published ends).
 //
 // CTAs [n_streams, grid) are workers: each claims work-ring positions one at a
-// time, runs the body for one (task, CTA index) unit, and the last CTA of a
-// task publishes done[slot] = seq + 1 with release semantics.
+// time, runs the body for one (task, CTA index) unit, then takes itself off
+// its slot's done word (seq + 1, CTAs still running) with a release reduction.
 //
 // Every wait is bounded by timeout_ns of no progress (a resident launch's
 // waits for the host by its idle limit); on expiry the waiter records
@@ -1200,8 +1200,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
-        // wait until every upstream task still active at dispatch retired: the
-        // task in slot b is seq - ((seq - b) mod W); done words only grow
+        // wait until every upstream task still active at dispatch completed: the
+        // task in slot b is seq - ((seq - b) mod W) (see slot_done)
         const unsigned long long up = s_up;
         if (up && threadIdx.x < 32) {
             const unsigned long long *done = P.done + stream * kMaxWindow;
@@ -1212,8 +1212,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             unsigned long long tw = 0;
             while (true) {
                 bool ok = true;
-                // acquire loads of the done words (released by the upstream
-                // tasks' last CTAs); the barrier below passes them to the CTA
+                // acquire loads of the done words (released by every CTA of the
+                // upstream tasks); the barrier below passes them to the CTA
                 if (w0) ok = slot_done(ld_acquire_u64(&done[lane]), i0);
                 if (w1) ok = ok && slot_done(ld_acquire_u64(&done[lane + 32]), i1);
                 if (__all_sync(0xffffffffu, ok)) break;
