@@ -211,9 +211,13 @@ typedef struct acs_stats {
     uint64_t sched_busy_cycles; /* ... of which spent inserting, retiring, dispatching */
     uint64_t sched_inserts;     /* tasks inserted into windows */
     uint64_t sched_iterations;  /* scheduler loop iterations */
-    uint64_t sched_phase_cycles[8]; /* scheduler-loop cycles by phase: descriptor loads,
-                                   inserts, retire, dispatch selection, ring-cell checks,
-                                   cell aux words, publication fence, cell stores */
+    uint64_t sched_phase_cycles[8]; /* ACS_FLAG_TRACE: scheduler-warp cycles by loop phase:
+                                   [0] loop top, [1] slot-state updates (with nothing to
+                                   insert: the room check), [2] retirement and in-order
+                                   release, [3] insertion (room, checked tasks, upstream
+                                   masks, work-ring offsets), [4] unused, [5] log and trace
+                                   entries, [6] hand-off to the publisher warp, [7] progress
+                                   and idle bookkeeping */
     uint64_t tasks_emitted;     /* tasks appended on the device by emit tasks */
     uint64_t device_seg_bytes;  /* segment bytes of every checked task (host- or device-submitted) */
     uint64_t check_cycles;      /* ACS_FLAG_TRACE: SM cycles the checker warps spent testing */
