@@ -360,7 +360,7 @@ class ClockSampler:
 class RLBench:
     """One mode (window / inorder / graph) on one device state."""
 
-    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False, span=0):
+    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False, span=0, traced=False):
         import torch
         import streamgen as sg
         from paper_2401_12377_b300 import harness
@@ -371,7 +371,7 @@ class RLBench:
         self.pristine = {k: v.clone() for k, v in self.bufs.t.items()}
         self.host_pinned = {k: torch.from_numpy(v.view("uint8").copy()).pin_memory() for k, v in host.items()}
         self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots,
-                                   span=span)
+                                   span=span, log=traced, trace=traced)
         self.emit = emit
         self.driver = (harness.RLEmitDriver if emit else harness.RLDriver)(self.sim, self.bufs, self.ctx)
         self.mode = mode
@@ -442,6 +442,97 @@ def time_arm(arm, steps, warmup, flush_buf, latencies=None):
     fixed = ("cta_slots", "grid")
     delta = {k: (st1[k] - st0[k]) if isinstance(st1[k], (int, float)) and k not in fixed else st1[k] for k in st1}
     return {"ms": ms, "tasks": tasks, "wall_s": wall, "stats": delta}
+
+
+def critical_path(ctx, stream: int, first: int, n: int):
+    """Longest chain of a stream's device-logged window DAG (every conflicting
+    predecessor within the ring span), each task weighted by its body time in a
+    traced run (first CTA start to last CTA end). Any legal schedule respects
+    these edges, so the chain bounds the run's makespan from below for zero
+    scheduling overhead. Returns (us, tasks on the chain)."""
+    span = ctx.span
+    masks, _, _ = ctx.log(stream, first, n)
+    tr = ctx.trace(stream, first, n).astype(np.int64)
+    body = np.maximum(tr[:, 3] - tr[:, 2], 0) / 1e3
+    fin = np.zeros(n)
+    cnt = np.zeros(n, np.int64)
+    for j in range(n):
+        m, seq = int(masks[j]), first + j
+        best, bc = 0.0, 0
+        while m:
+            b = (m & -m).bit_length() - 1
+            m &= m - 1
+            i = j - (seq - b) % span           # the predecessor in slot b
+            if 0 <= i < j and fin[i] > best:
+                best, bc = fin[i], cnt[i]
+        fin[j] = best + body[j]
+        cnt[j] = bc + 1
+    k = int(np.argmax(fin)) if n else 0
+    return (float(fin[k]), int(cnt[k])) if n else (0.0, 0)
+
+
+def task_segments(rows):
+    """Read and write segments of packed task rows, as the library resolves
+    them (acs_get_addresses)."""
+    from paper_2401_12377_b300 import acs
+    return [acs.acs_get_addresses(acs.acs_args.from_buffer_copy(r.tobytes())) for r in rows]
+
+
+def critical_path_full(segs, body_us):
+    """Longest chain of a stream's full dependency DAG (every read-after-write,
+    write-after-read and write-after-write pair, however far apart), tasks
+    weighted by body_us. Per byte it keeps the finish time of its last writer
+    and the latest finish of its readers since: a read waits for the writer, a
+    write for both, and older conflicts are implied through them. Returns
+    (us, tasks on the chain)."""
+    import bisect
+    whole = (0, (1 << 64) - 1)
+    ranges = sorted((s, s + n) for rd, wr in segs for s, n in list(rd) + list(wr) if n and (s, n) != whole)
+    merged = []
+    for a, b in ranges:
+        if merged and a <= merged[-1][1]:
+            merged[-1][1] = max(merged[-1][1], b)
+        else:
+            merged.append([a, b])
+    starts = [a for a, _ in merged]
+    base, off = [], 0
+    for a, b in merged:
+        base.append(off)
+        off += b - a
+    lw, rd = np.zeros(off), np.zeros(off)                  # finish times (us)
+    lwc, rdc = np.zeros(off, np.int64), np.zeros(off, np.int64)   # chain lengths
+
+    def slices(seg_list):
+        out = []
+        for s, n in seg_list:
+            if (s, n) == whole:
+                out.append(slice(0, off))
+            elif n:
+                k = bisect.bisect_right(starts, s) - 1
+                lo = base[k] + (s - merged[k][0])
+                out.append(slice(lo, lo + n))
+        return out
+
+    best_all, cnt_all = 0.0, 0
+    for (r, w), body in zip(segs, body_us):
+        rs, ws = slices(r), slices(w)
+        best, bc = 0.0, 0
+        for sl, arrs in [(x, ((lw, lwc),)) for x in rs] + [(x, ((lw, lwc), (rd, rdc))) for x in ws]:
+            for arr, carr in arrs:
+                if sl.stop > sl.start:
+                    k = int(np.argmax(arr[sl]))
+                    if arr[sl][k] > best:
+                        best, bc = float(arr[sl][k]), int(carr[sl][k])
+        f, c = best + float(body), bc + 1
+        for sl in rs:
+            upd = rd[sl] < f
+            rd[sl][upd] = f
+            rdc[sl][upd] = c
+        for sl in ws:
+            lw[sl], lwc[sl], rd[sl], rdc[sl] = f, c, 0.0, 0
+        if f > best_all:
+            best_all, cnt_all = f, c
+    return best_all, cnt_all
 
 
 def time_e2e(arm, steps):
@@ -832,6 +923,15 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     wl.bind(ctx1)
     res1 = time_arm(BatchArm(torch, wl, ctx1), max(1, min(args.steps, 3)), 1, flush_buf)
     ctx1.close()
+    # the DAG's critical path: one traced single-flush pass, outside the timed
+    # regions; the pass is bounded by its longest stream chain
+    ctx_t = harness.Context(W, n_streams=S, cta_slots=slots, capacity=cap, log=True, trace=True)
+    wl.bind(ctx_t)
+    wl.reset()
+    wl.run()
+    cps = [critical_path(ctx_t, i, 0, ctx_t.tail(i)) for i in range(S)]
+    ctx_t.close()
+    cp_i = max(range(S), key=lambda i: cps[i][0])
     # the method: a resident kernel, each stream published as soon as it is
     # submitted (longest first); a pass ends when every stream is idle. CUDA
     # events on this stream bracket each pass (the pass is host-synchronous).
@@ -863,6 +963,11 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
+            "critical_path": {"us": cps[cp_i][0], "tasks_on_chain": cps[cp_i][1], "stream": cp_i,
+                              "kernel_us_per_pass": avg_launch_s * 1e6,
+                              "note": "the longest of the 64 streams' chains (logged window DAG, tasks "
+                                      "weighted by their body times in a traced pass): the makespan with "
+                                      "no scheduling overhead"},
             "config": {"workload": WORKLOAD_BATCHED, "streams": S, "window": W, "tasks_per_step": tasks_per_step,
                        "cta_slots": st.get("cta_slots"), "grid": st.get("grid"),
                        "stream_lengths": [sp.target for sp in specs],
@@ -1110,6 +1215,24 @@ def main():
             "sched_cycles_per_task": st["sched_cycles"] / max(1, st["sched_inserts"]),
             "gpu_launches": int(launches),
             "clocks": clocks}
+
+    # ---- the DAG's critical path (a traced run outside the timed region) ----------------------
+    # Nearly every conflict of this stream is W or more positions apart (a
+    # step's broadphase and integrate tasks sit beyond the window from its
+    # solves), so the chain is taken over the full DAG of the host-driven form
+    # of the stream, whose every task the host knows
+    ta = RLBench("window", seed, args.window, args.cta_slots, emit=False, traced=True)
+    ta.reset_device()
+    plans = ta.driver.run(record_plans=True)
+    n_t = ta.ctx.tail(0)
+    tr_t = ta.ctx.trace(0, 0, n_t).astype(np.int64)
+    rows = np.concatenate([ta.driver.pack(p)[1] for p in plans])
+    ta.ctx.close()
+    cp_us, cp_n = critical_path_full(task_segments(rows), np.maximum(tr_t[:, 3] - tr_t[:, 2], 0) / 1e3)
+    line["critical_path"] = {"us": cp_us, "tasks_on_chain": cp_n, "kernel_us_per_run": avg_launch_s * 1e6,
+                             "note": "longest chain of the full dependency DAG of the stream's host-driven "
+                                     "form (no emit tasks), tasks weighted by their body times in a traced "
+                                     "run: the makespan with no scheduling overhead"}
 
     # ---- baselines on the same box -----------------------------------------------------------
     if not args.no_baselines:

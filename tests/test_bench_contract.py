@@ -1,10 +1,12 @@
-"""bench.py's reference arm on the CPU: one JSON line with the keys the
-benchmark contract requires, for the default workload and a per-input one."""
+"""bench.py on the CPU: the reference arm's one JSON line with the keys the
+benchmark contract requires (the default workload and a per-input one), and
+the critical-path bound computed from a logged DAG."""
 import json
 import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,3 +28,69 @@ def test_reference_arm_json_line(workload):
     assert line["higher_is_better"] is True and line["n_gpus"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"]
+
+
+class _FakeCtx:
+    """Stands in for a traced context: logged masks (bit = predecessor's slot,
+    seq mod span) and trace rows for a hand-made DAG."""
+
+    def __init__(self, span, first, edges, body_us):
+        self.span, self.first = span, first
+        n = len(body_us)
+        self.masks = np.zeros(n, np.uint64)
+        for i, j in edges:
+            self.masks[j] |= np.uint64(1 << ((first + i) % span))
+        self.tr = np.zeros((n, 5), np.uint64)
+        self.tr[:, 2] = 1000
+        self.tr[:, 3] = 1000 + (np.array(body_us) * 1000).astype(np.uint64)
+
+    def log(self, stream, first, n):
+        assert first == self.first and n == len(self.masks)
+        return self.masks, None, None
+
+    def trace(self, stream, first, n):
+        return self.tr
+
+
+@pytest.mark.parametrize("first", [0, 6, 13])
+def test_critical_path_of_a_logged_dag(first):
+    import bench
+    # 0->1->3->5, 2->3->5, 4->5 with bodies 1, 2, 5, 1, 1, 1 us: the longest
+    # chain is 2 -> 3 -> 5 (7 us, 3 tasks)
+    ctx = _FakeCtx(4, first, [(0, 1), (1, 3), (2, 3), (3, 5), (4, 5)], [1, 2, 5, 1, 1, 1])
+    us, k = bench.critical_path(ctx, 0, first, 6)
+    assert abs(us - 7.0) < 1e-9 and k == 3
+    # no edges: the longest single body
+    ctx = _FakeCtx(4, first, [], [1, 2, 5, 1, 1, 1])
+    assert bench.critical_path(ctx, 0, first, 6) == (5.0, 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_full_dag_critical_path_against_brute_force(seed):
+    """bench.critical_path_full (per-byte last writer / readers) against the
+    longest path over the oracle's all-pairs DAG E, on random small streams
+    with read-write ranges, zero-size segments and distant conflicts."""
+    import bench
+    from oracle import deps
+    rng = np.random.default_rng(seed)
+    base = 1 << 30
+    segs, body = [], []
+    for _ in range(120):
+        def one():
+            return (base + int(rng.integers(0, 4096)) * 4 * (1 + seed % 2), int(rng.integers(0, 65)) * 4)
+        rd = [one() for _ in range(int(rng.integers(0, 4)))]
+        wr = [one() for _ in range(int(rng.integers(0 if rd else 1, 3)))]
+        if wr and rng.random() < 0.3:
+            rd.append(wr[0])                        # a read-modify-write range
+        segs.append((rd, wr))
+        body.append(float(rng.integers(1, 50)))
+    E = deps.full_dag(segs)
+    preds = {}
+    for i, j in E:
+        preds.setdefault(j, []).append(i)
+    fin = []
+    for j in range(len(segs)):
+        fin.append(body[j] + max((fin[i] for i in preds.get(j, [])), default=0.0))
+    us, k = bench.critical_path_full(segs, body)
+    assert abs(us - max(fin)) < 1e-9
+    assert 1 <= k <= len(segs)
