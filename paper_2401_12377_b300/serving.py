@@ -22,7 +22,7 @@ from __future__ import annotations
 import collections
 import time
 from dataclasses import dataclass, field
-from typing import Dict, List, Optional
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 import torch
@@ -160,6 +160,22 @@ class _Live:
     admitted: float
 
 
+def admit_fifo(waiting, free, in_use: int, budget: int, need) -> List[Tuple[int, int]]:
+    """Admission, oldest first: the head of the `waiting` queue takes a slot
+    from `free` while one is free and its bytes (`need(request)`) fit the
+    budget beside `in_use`; the first request that does not fit stops the
+    round, so no later request overtakes it. Pops what it admits and returns
+    [(request, slot)]."""
+    out = []
+    while waiting and free:
+        nb = need(waiting[0])
+        if in_use + nb > budget:
+            break
+        out.append((waiting.popleft(), free.popleft()))
+        in_use += nb
+    return out
+
+
 class Server:
     """The request loop over one resident context (n_streams = slots)."""
 
@@ -249,12 +265,9 @@ class Server:
                     last_done = last_move = t
             # admissions, oldest first
             batch = []
-            while waiting and free:
-                e = cat.entries[int(kinds[waiting[0]])]
-                if in_use + e.nbytes > self.budget:
-                    break
-                i = waiting.popleft()
-                s = free.popleft()
+            for i, s in admit_fifo(waiting, free, in_use, self.budget,
+                                   lambda r: cat.entries[int(kinds[r])].nbytes):
+                e = cat.entries[int(kinds[i])]
                 blk = torch.empty(e.nbytes, dtype=torch.uint8, device="cuda")
                 base = np.uint64(blk.data_ptr())
                 packed = e.packed.copy()
