@@ -128,7 +128,8 @@ typedef struct { uint64_t pos, vel, prop; uint32_t nenv; float dt, gdt, box; } a
  * t + 1 < steps one ACS_OP_RL_BROADPHASE per chunk of step t + 1 followed by
  * the emit task of step t + 1. Appended tasks get task_id = their position in
  * the stream. Chunk CTA counts come from ncta_table[(t * 2 + k) * n_chunks + c]
- * (k = 0 broadphase of step t, k = 1 integrate of step t). Segments: reads
+ * (k = 0 broadphase of step t, k = 1 integrate of step t; bytes, each 1 .. 255:
+ * the device does not check them, a 0 would leave that task unrun). Segments: reads
  * nisl, the cfg block and the table; writes the 4-byte token (so emit tasks of
  * one stream are ordered). A stream holding an emit task stays open until the
  * last emit task ran: acs_sync returns once every appended task retired. */

@@ -344,7 +344,10 @@ class RLEmitDriver:
         for k in ("dt", "gdt", "box"):
             cfg[k] = sc["rl_integrate"][k]
         self.cfg = torch.from_numpy(cfg.view(np.uint8).copy()).to("cuda")
-        self.table = torch.from_numpy(sim.ncta_table()).to("cuda")
+        table = sim.ncta_table()
+        if table.size and int(table.min()) < 1:      # the device takes these CTA counts as they are
+            raise ValueError("ncta_table entries must be 1 .. 255")
+        self.table = torch.from_numpy(table).to("cuda")
         self._packed = None   # the first tasks' rows: the same every run, ids aside
 
     def first_tasks(self):
