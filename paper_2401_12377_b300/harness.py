@@ -333,6 +333,9 @@ class RLEmitDriver:
     flush, one persistent launch and one sync."""
 
     def __init__(self, sim, bufs: DeviceBuffers, ctx: Context, stream: int = 0):
+        table = sim.ncta_table()
+        if table.size and int(table.min()) < 1:      # the device takes these CTA counts as they are
+            raise ValueError("ncta_table entries must be 1 .. 255")
         self.sim, self.bufs, self.ctx, self.stream = sim, bufs, ctx, stream
         p = sim.p
         sc = sim.scalars()
@@ -344,9 +347,6 @@ class RLEmitDriver:
         for k in ("dt", "gdt", "box"):
             cfg[k] = sc["rl_integrate"][k]
         self.cfg = torch.from_numpy(cfg.view(np.uint8).copy()).to("cuda")
-        table = sim.ncta_table()
-        if table.size and int(table.min()) < 1:      # the device takes these CTA counts as they are
-            raise ValueError("ncta_table entries must be 1 .. 255")
         self.table = torch.from_numpy(table).to("cuda")
         self._packed = None   # the first tasks' rows: the same every run, ids aside
 

@@ -1,4 +1,4 @@
-"""The serving loop's admission policy on the CPU (no device): oldest first,
+"""Host-side checks on the CPU (no device). The serving loop's admission policy: oldest first,
 a free stream slot and the device budget both required, and no request
 overtakes the head of the queue."""
 import collections
@@ -33,3 +33,22 @@ def test_nothing_waiting_or_no_slot():
     assert admit_fifo(_q([]), _q([0]), 0, 10, lambda r: 1) == []
     w = _q([0])
     assert admit_fifo(w, _q([]), 0, 10, lambda r: 1) == [] and list(w) == [0]
+
+
+def test_emit_driver_rejects_a_zero_cta_count():
+    """A device emitter takes its chunk CTA counts from the table as they are,
+    so the host driver refuses a table with a 0 before anything reaches the
+    device."""
+    import numpy as np
+    import pytest
+    import streamgen as sg
+    from paper_2401_12377_b300 import harness
+
+    class Sim(sg.RLSim):
+        def ncta_table(self):
+            t = super().ncta_table()
+            t[3] = 0
+            return t
+
+    with pytest.raises(ValueError, match="ncta_table"):
+        harness.RLEmitDriver(Sim(1, sg.RLParams(n_env=16, steps=2)), bufs=None, ctx=None)
