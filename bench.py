@@ -76,9 +76,9 @@ def parse():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
-# launch of the default workload, from the ncu capture summarised in
-# profiles/acs_persistent_kernel_rlsim_full.md; it applies only while the
-# kernel's sources hash to the value it was taken with (else traffic is null).
+# launch of the default workload, from one ncu capture of that launch; it
+# applies only while the kernel's sources hash to the value it was taken with
+# (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
 TRAFFIC_RLSIM = {"bytes_per_launch": 3639552, "sources_sha1": "c52ed274a495cc17a86afb0cb3554b364afabc86"}

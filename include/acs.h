@@ -129,7 +129,8 @@ typedef struct { uint64_t pos, vel, prop; uint32_t nenv; float dt, gdt, box; } a
  * the emit task of step t + 1. Appended tasks get task_id = their position in
  * the stream. Chunk CTA counts come from ncta_table[(t * 2 + k) * n_chunks + c]
  * (k = 0 broadphase of step t, k = 1 integrate of step t; bytes, each 1 .. 255:
- * the device does not check them, a 0 would leave that task unrun). Segments: reads
+ * an emit task that finds a 0 among the entries it copies appends nothing and
+ * fails the launch with ACS_ERR_INVALID, returned by acs_sync). Segments: reads
  * nisl, the cfg block and the table; writes the 4-byte token (so emit tasks of
  * one stream are ordered). A stream holding an emit task stays open until the
  * last emit task ran: acs_sync returns once every appended task retired. */
@@ -370,6 +371,25 @@ int acs_start(acs_ctx *ctx);
 int acs_progress(acs_ctx *ctx, uint32_t *head, uint32_t *idle_at);   /* arrays of n_streams, either NULL */
 int acs_stop(acs_ctx *ctx);
 
+/*
+ * acs_abort -- stop the context's work from the host (window mode).
+ *
+ * Raises the device stop word of the context: every wait of a running
+ * persistent launch (scheduler, workers, task bodies that poll it) ends, and
+ * the launch exits without running the tasks it had not started. The context's
+ * error becomes ACS_ERR_STOPPED (sticky): acs_sync returns it once the launch
+ * has ended, and acs_submit / acs_flush return it from then on; destroy the
+ * context and create a new one to run more work. Other CUDA work and other
+ * contexts are unaffected. The stop word is written by a copy on a
+ * non-blocking stream of the call's own, so the call never waits behind the
+ * running kernel; it returns once the word is written. Unlike every other
+ * entry point it may be called from a host thread other than the context's
+ * owner (e.g. a watchdog while the owner blocks in acs_sync), and with no
+ * launch in flight. Errors: ACS_ERR_INVALID (NULL, or a mode other than
+ * ACS_MODE_WINDOW), ACS_ERR_DEVICE (the copy failed).
+ */
+int acs_abort(acs_ctx *ctx);
+
 /* Copy the context's counters into *out (after acs_sync for device figures). */
 int acs_get_stats(acs_ctx *ctx, acs_stats *out);
 
@@ -381,30 +401,35 @@ int acs_graph_replay(acs_ctx *ctx);
  * acs_run_noalloc -- run one stream of tasks without allocating anything.
  *
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory where they run their tasks, e.g. code executing
- * during CUDA graph capture (allocation is not capturable), code embedded in a
- * framework that owns the memory budget, or paths that cannot absorb an
- * allocator's latency or failure. It runs the same persistent scheduler kernel
- * as acs_flush (window of `window` slots, one stream, tasks in program order
- * with the segments acs_get_addresses derives), but every byte of scratch
- * comes from one fixed-size array in the library's device memory that every
- * GPU loading the library holds until exit (under 2 MiB).
+ * cannot allocate device memory where they run their tasks, e.g. code embedded
+ * in a framework that owns the device memory budget and forbids side
+ * allocations, or paths that cannot absorb an allocator's latency or failure.
+ * It runs the same persistent scheduler kernel as acs_flush (window of
+ * `window` slots, one stream, tasks in program order with the segments
+ * acs_get_addresses derives), but every byte of scratch comes from one
+ * fixed-size array in the library's device memory that every GPU loading the
+ * library holds until exit (under 2 MiB).
  *
  *   window      1 .. ACS_MAX_WINDOW
  *   n           number of tasks, 0 .. ACS_NOALLOC_MAX_TASKS (more: ACS_ERR_INVALID)
  *   task_ids    n strictly increasing ids (host memory)
  *   args        n packed tasks (host memory); their pointers name the caller's
- *               device buffers, which are the inputs and outputs
+ *               device buffers, which are the inputs and outputs. Every op but
+ *               ACS_OP_RL_EMIT (which needs a context's emitter state).
  *   cuda_stream cudaStream_t to run on (NULL: the legacy default stream)
  *
- * Blocks until the tasks retired; returns ACS_OK or the first error
- * (ACS_ERR_INVALID / ACS_ERR_ORDER for bad tasks, ACS_ERR_TIMEOUT,
+ * Every task is checked on the host before anything reaches the device:
+ * ACS_ERR_INVALID for an unknown op, an emit task, ncta outside
+ * 1 .. ACS_MAX_NCTA, a nonzero reserved word or a bad segment; ACS_ERR_ORDER
+ * for ids that do not increase; ACS_ERR_INVALID, before the stream is used,
+ * if `cuda_stream` is in capture mode. The call then blocks until the tasks
+ * retired (it synchronizes `cuda_stream` and copies the error word back) and
+ * returns ACS_OK or the first device error (ACS_ERR_TIMEOUT, ACS_ERR_INVALID from a device self-check,
  * ACS_ERR_DEVICE). The first call on a device resolves the array's device
- * address and sets the kernel's attributes with that device current: make it
- * before any stream capture. Calls share the array (each re-initialises what
- * must start at zero); calls whose device work overlaps race on it and must not
- * be made. Not thread-safe. Calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * address and sets the kernel's attributes with that device current. Calls
+ * share the array (each re-initialises what must start at zero); calls whose
+ * device work overlaps race on it and must not be made. Not thread-safe. Calls
+ * no cudaMalloc, cudaFree or other allocating routine.
  */
 #define ACS_NOALLOC_MAX_TASKS 4096
 int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task_ids, const acs_args *args,

@@ -72,14 +72,14 @@ class acs_stats(C.Structure):
                 ("grid", C.c_uint32)]
 
 
-# numpy image of acs_args (64 bytes) for packing many tasks at once
+# numpy image of acs_args (56 bytes) for packing many tasks at once
 ARGS_DTYPE = np.dtype([("op", "<u2"), ("ncta", "<u2"), ("reserved", "<u4"), ("bytes", "V48")])
 assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
            "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_stream_tail",
            "acs_get_stats", "acs_graph_replay", "acs_start", "acs_progress", "acs_stop",
-           "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc"]
+           "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc", "acs_abort"]
 
 _lib = None
 
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.acs_progress.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.acs_stop.argtypes = [C.c_void_p]
     lib.acs_error.argtypes = [C.c_void_p]
+    lib.acs_abort.argtypes = [C.c_void_p]
     lib.acs_strerror.argtypes = [C.c_int]
     lib.acs_strerror.restype = C.c_char_p
     lib.acs_run_noalloc.argtypes = [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -247,6 +248,11 @@ def acs_graph_replay(ctx) -> int:
 
 def acs_error(ctx) -> int:
     return load().acs_error(ctx)
+
+
+def acs_abort(ctx) -> int:
+    """Raise the context's device stop word (any host thread); see include/acs.h."""
+    return load().acs_abort(ctx)
 
 
 def acs_strerror(code: int) -> str:

@@ -1041,6 +1041,20 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     }
     const uint32_t n_solve = count;
     const uint32_t n_new = n_solve + n_chunks + (more ? n_chunks + 1 : 0);
+    // the chunk CTA counts this task copies from the table must be 1 .. 255 (a
+    // 0 would leave its task unrun): checked before anything is appended
+    const uint8_t *table = reinterpret_cast<const uint8_t *>(a.ncta_table);
+    {
+        bool bad = false;
+        for (uint32_t c = tid; c < n_chunks; c += kBlock) {
+            bad |= table[(a.step * 2 + 1) * n_chunks + c] == 0;
+            if (more) bad |= table[((a.step + 1) * 2 + 0) * n_chunks + c] == 0;
+        }
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteEmit);
+            return;
+        }
+    }
     // position of the first new task; wait (bounded) until the ring positions
     // it overwrites hold only released tasks no window still looks at
     if (tid == 0) {
@@ -1065,7 +1079,6 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     if (!E.ok) return;
     const uint32_t base = E.base;
     const acs_rl_emit_cfg &cfg = E.cfg;
-    const uint8_t *table = reinterpret_cast<const uint8_t *>(a.ncta_table);
     constexpr uint64_t kPos = 32 * 3 * 4, kProp = 32 * 2 * 4, kRec = ACS_RL_REC_BYTES;
     for (uint32_t k = tid; k < n_new; k += kBlock) {
         const uint32_t seq = base + k;

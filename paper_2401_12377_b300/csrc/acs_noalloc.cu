@@ -1,22 +1,25 @@
 // acs_run_noalloc: the window scheduler for callers that must not allocate.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the point
-// where they want to run a batch of tasks: code that runs while a CUDA graph is
-// being captured (allocation calls are not capturable), code inside another
-// framework that owns the device memory budget and forbids side allocations,
-// or latency-critical paths that cannot absorb an allocator's cost or failure.
+// where they want to run a batch of tasks: code inside another framework that
+// owns the device memory budget and forbids side allocations, or
+// latency-critical paths that cannot absorb an allocator's cost or failure.
 // For them this entry point runs one stream of tasks through the same
 // persistent scheduler kernel as acs_flush, but takes every byte of scratch
 // (descriptor ring, work ring, counters, status) from one file-scope device
 // array that exists for as long as the library is loaded. The caller provides
 // only the tasks; their data buffers stay the caller's.
 //
+// The call blocks: it synchronizes the caller's stream and reads the error
+// word back. A stream in capture mode is refused (ACS_ERR_INVALID) before the
+// call uses it.
+//
 // The array is a host-side symbol: its device address is obtained once per
 // device with cudaGetSymbolAddress (with that device current) on the first
-// call on that device, so that first call should happen before any stream
-// capture. Every call shares the array and finds the previous call's contents;
-// each call re-initialises what must start from zero. Calls whose device work
-// overlaps (e.g. on two streams) race on the array and must not be issued.
+// call on that device. Every call shares the array and finds the previous
+// call's contents; each call re-initialises what must start from zero. Calls
+// whose device work overlaps (e.g. on two streams) race on the array and must
+// not be issued.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -34,7 +37,12 @@ using namespace acs;
 namespace {
 
 constexpr uint32_t kNoAllocCapLog2 = 12;                 // descriptor ring: ACS_NOALLOC_MAX_TASKS
-constexpr uint32_t kNoAllocCells = 16384;                // work-ring cells
+// work-ring cells: up to (2W - 1) tasks of ACS_MAX_NCTA units each can be in
+// flight (W inserted, W - 1 more checked and waiting), rounded up to a power of two
+constexpr uint32_t pow2_at_least(uint32_t x) { return x <= 1u ? 1u : 2u * pow2_at_least((x + 1u) / 2u); }
+constexpr uint32_t kNoAllocCells = pow2_at_least((2u * ACS_MAX_WINDOW - 1u) * ACS_MAX_NCTA);
+static_assert((kNoAllocCells & (kNoAllocCells - 1u)) == 0 && kNoAllocCells >= (2u * ACS_MAX_WINDOW - 1u) * ACS_MAX_NCTA,
+              "work ring holds every unit that can be in flight");
 constexpr size_t kAlign = 256;
 
 constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -117,21 +125,18 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     if (n > ACS_NOALLOC_MAX_TASKS) return ACS_ERR_INVALID;   // beyond the scratch array's capacity
     if (n && (!task_ids || !args)) return ACS_ERR_INVALID;
     if (n == 0) return ACS_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ACS_ERR_DEVICE;
-    DeviceSetup &d = g_setup[dev];
-    int rc = setup_device(dev, d);
-    if (rc) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // descriptors (the same layout acs_submit writes), checked as acs_submit does
+    // descriptors (the same layout acs_submit writes), checked as acs_submit
+    // does, on the host before anything reaches the device. Emit tasks need a
+    // context's per-stream emitter words, which this entry point does not
+    // have: they are refused.
     for (uint32_t i = 0; i < n; ++i) {
         const acs_args &a = args[i];
-        if (a.ncta < 1 || a.ncta > ACS_MAX_NCTA || a.reserved) return ACS_ERR_INVALID;
+        if (a.ncta < 1 || a.ncta > ACS_MAX_NCTA || a.reserved || a.op == ACS_OP_RL_EMIT) return ACS_ERR_INVALID;
         if (i && task_ids[i] <= task_ids[i - 1]) return ACS_ERR_ORDER;
         acs_segment rd[ACS_MAX_SEGS], wr[ACS_MAX_SEGS];
         uint32_t nr = 0, nw = 0;
-        if (acs_get_addresses(&a, rd, &nr, wr, &nw) != ACS_OK) return ACS_ERR_INVALID;
+        if (acs_get_addresses(&a, rd, &nr, wr, &nw) != ACS_OK) return ACS_ERR_INVALID;   // unknown op too
         TaskRec &r = g_stage[i];
         std::memset(&r, 0, sizeof r);
         uint32_t cnt = 0;
@@ -147,6 +152,17 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
         r.seq = i;
         std::memcpy(r.args, a.bytes, sizeof r.args);
     }
+
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the call synchronizes and copies back: a stream in capture mode is refused
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return ACS_ERR_DEVICE;
+    if (cap != cudaStreamCaptureStatusNone) return ACS_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ACS_ERR_DEVICE;
+    DeviceSetup &d = g_setup[dev];
+    int rc = setup_device(dev, d);
+    if (rc) return rc;
 
     unsigned char *base = d.scratch;
     TaskRec *ring = reinterpret_cast<TaskRec *>(base + kOffRing);

@@ -116,6 +116,7 @@ struct acs_ctx {
     uint32_t *h_one = nullptr;           // pinned source of those copies
     std::vector<StreamState> st;
     int err = ACS_OK;
+    uint32_t aborted = 0;                // acs_abort was called (atomic: any host thread)
     uint32_t grid = 0, cta_slots = 0, smem = 0;
     acs_stats stats{};
     std::vector<TimedLaunch> timed;     // launches whose events are not yet read
@@ -320,6 +321,7 @@ int resident_status(acs_ctx *c) {
     const uint32_t e = __atomic_load_n(&c->h_mbox->err, __ATOMIC_ACQUIRE);
     if (e) return fail(c, (int)(int32_t)e);
     if (__atomic_load_n(&c->h_mbox->expired, __ATOMIC_ACQUIRE)) return fail(c, ACS_ERR_STOPPED);
+    if (__atomic_load_n(&c->aborted, __ATOMIC_ACQUIRE)) return fail(c, ACS_ERR_STOPPED);
     return ACS_OK;
 }
 
@@ -951,6 +953,7 @@ int acs_submit_ops(acs_ctx *c, uint32_t stream, uint32_t n, const uint32_t *task
 
 int acs_flush(acs_ctx *c) {
     if (!c) return ACS_ERR_INVALID;
+    if (__atomic_load_n(&c->aborted, __ATOMIC_ACQUIRE)) fail(c, ACS_ERR_STOPPED);
     if (c->err) return c->err;
     uint32_t n = 0;
     for (auto &s : c->st) n += s.submitted - s.flushed;
@@ -1017,6 +1020,7 @@ int acs_sync(acs_ctx *c) {
     if (c->cfg.mode == ACS_MODE_WINDOW) {
         const uint32_t derr = c->h_status->err;
         if (derr) fail(c, (int)(int32_t)derr);
+        if (__atomic_load_n(&c->aborted, __ATOMIC_ACQUIRE)) fail(c, ACS_ERR_STOPPED);
     }
     if (c->cfg.mode == ACS_MODE_GRAPH) release_graphs(c, true);
     if (c->err) return c->err;
@@ -1219,6 +1223,27 @@ int acs_stop(acs_ctx *c) {
     }
     if (!c->err && __atomic_load_n(&c->h_mbox->expired, __ATOMIC_ACQUIRE)) return ACS_ERR_STOPPED;
     return c->err;
+}
+
+int acs_abort(acs_ctx *c) {
+    if (!c) return ACS_ERR_INVALID;
+    if (c->cfg.mode != ACS_MODE_WINDOW) return ACS_ERR_INVALID;
+    __atomic_store_n(&c->aborted, 1u, __ATOMIC_RELEASE);
+    // the device stop word, written by the copy engine on a stream of this
+    // call's own (non-blocking, so it never waits behind the running kernel)
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return ACS_ERR_DEVICE;
+    if (prev != c->device && cudaSetDevice(c->device) != cudaSuccess) return ACS_ERR_DEVICE;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(&c->d_ctl->stop, c->h_one, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+        const cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (prev != c->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? ACS_OK : ACS_ERR_DEVICE;
 }
 
 int acs_stream_tail(acs_ctx *c, uint32_t stream, uint32_t *tail) {

@@ -191,6 +191,60 @@ def dnn_stream(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
     return Stream(bufs, tasks, window, f"dnn(seed={seed},batch={batch})")
 
 
+def dnn_stream_unrolled(seed: int, batch: int = 1, blocks: int = 24, hidden: int = 256,
+                        window: int = 32) -> Stream:
+    """The computation of ``dnn_stream(seed, batch, blocks, hidden)`` with every
+    intermediate kept, so that each task can be re-evaluated on its own inputs
+    afterwards. Block k of sample s (when its gate runs it) is six tasks:
+    ``p = W1_k h`` (GEMV into a fresh range), ``t = 1 * p`` (scale: a copy),
+    ``t = relu(t + b1_k)``, ``u = W2_k t`` (GEMV, fresh), ``h' = 1 * h`` (copy
+    into the next hidden-state slot) and ``h' = h' + (u + b2_k)``. Weights,
+    biases, inputs, gates and GEMV CTA counts are those of ``dnn_stream``, and
+    the copies are exact, so sample s's last hidden-state slot holds what
+    ``dnn_stream`` leaves in its ``h``. Buffers: ``h`` [batch][blocks + 1][H]
+    (slot 0 the input), ``p``, ``t``, ``u`` [batch][blocks][H]."""
+    rng = np.random.default_rng(seed)
+    H = hidden
+    W = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H, H)).astype(np.float32)
+    B = rng.uniform(-1.0 / 16, 1.0 / 16, (blocks, 2, H)).astype(np.float32)
+    h0 = rng.uniform(-1.0, 1.0, (batch, H)).astype(np.float32)
+    h = np.zeros((batch, blocks + 1, H), np.float32)
+    h[:, 0] = h0
+    z = np.zeros(batch * blocks * H, np.float32)
+    bufs = {"W": W.reshape(-1), "B": B.reshape(-1), "h": h.reshape(-1), "p": z, "t": z.copy(), "u": z.copy()}
+    one = np.float32(1.0)
+    dims = {"m": np.uint32(H), "k": np.uint32(H)}
+    cur = [0] * batch
+    tasks: List[Task] = []
+
+    def add(op, ncta, arrays, scalars=None):
+        tasks.append(Task(len(tasks), op, ncta, arrays, dict(scalars or {})))
+
+    for k in range(blocks):
+        for s in range(batch):
+            if not dnn_gate(seed, s, k):
+                continue
+            w1 = Ref("W", (k * 2 + 0) * H * H, H * H)
+            w2 = Ref("W", (k * 2 + 1) * H * H, H * H)
+            b1 = Ref("B", (k * 2 + 0) * H, H)
+            b2 = Ref("B", (k * 2 + 1) * H, H)
+            hs = Ref("h", (s * (blocks + 1) + cur[s]) * H, H)
+            hn = Ref("h", (s * (blocks + 1) + k + 1) * H, H)
+            ps, ts, us = (Ref(n, (s * blocks + k) * H, H) for n in ("p", "t", "u"))
+            c1 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 1) % len(GEMV_NCTA_CHOICES)]
+            c2 = GEMV_NCTA_CHOICES[mix(seed, 0x61, s, k, 2) % len(GEMV_NCTA_CHOICES)]
+            add("gemv", c1, {"W": w1, "x": hs, "y": ps}, dims)
+            add("scale", 1, {"x": ps, "y": ts}, {"a": one})
+            add("bias_relu", 1, {"t": ts, "b": b1})
+            add("gemv", c2, {"W": w2, "x": ts, "y": us}, dims)
+            add("scale", 1, {"x": hs, "y": hn}, {"a": one})
+            add("resid", 1, {"h": hn, "u": us, "b": b2})
+            cur[s] = k + 1
+    st = Stream(bufs, tasks, window, f"dnn_unrolled(seed={seed},batch={batch})")
+    st.last_slot = list(cur)
+    return st
+
+
 # ----------------------------------------------------------------------------
 # Static irregular DAG (randomly wired network of small GEMVs)
 # ----------------------------------------------------------------------------

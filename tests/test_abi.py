@@ -109,4 +109,75 @@ def test_init_without_a_gpu_fails_cleanly(lib):
     h = C.c_void_p()
     assert lib.acs_init(C.byref(h), 8, None) == acs.ACS_ERR_DEVICE
     assert lib.acs_flush(None) == acs.ACS_ERR_INVALID
+    assert lib.acs_abort(None) == acs.ACS_ERR_INVALID
     lib.acs_destroy(None)
+
+
+def _noalloc_rows(specs):
+    """Packed rows for acs_run_noalloc: (op, ncta, fields) per task."""
+    import numpy as np
+    from paper_2401_12377_b300.harness import _args_row
+    return np.concatenate([_args_row(op, ncta, f) for op, ncta, f in specs])
+
+
+_AXPY = {"x": 4096, "y": 8192, "n": 16, "a": 2.0}
+_EMIT = {"cfg": 4096, "nisl": 8192, "token": 12288, "ncta_table": 16384, "n_env": 8, "step": 0, "steps": 2,
+         "chunk": 4}
+
+
+@pytest.mark.parametrize("case,expect", [
+    ("ids_equal", acs.ACS_ERR_ORDER),
+    ("ids_decrease", acs.ACS_ERR_ORDER),
+    ("unknown_op", acs.ACS_ERR_INVALID),
+    ("ncta_0", acs.ACS_ERR_INVALID),
+    ("ncta_257", acs.ACS_ERR_INVALID),
+    ("reserved", acs.ACS_ERR_INVALID),
+    ("emit_task", acs.ACS_ERR_INVALID),
+    ("segment_overflow", acs.ACS_ERR_INVALID),
+])
+def test_noalloc_refuses_bad_tasks_on_the_host(lib, case, expect):
+    """acs_run_noalloc checks every task before it touches the device, so each
+    refusal below comes back on a machine without a GPU as on one with a GPU."""
+    import numpy as np
+    ids = np.array([1, 2, 3], np.uint32)
+    specs = [("axpy", 1, _AXPY)] * 3
+    if case == "ids_equal":
+        ids = np.array([1, 2, 2], np.uint32)
+    elif case == "ids_decrease":
+        ids = np.array([5, 4, 6], np.uint32)
+    elif case == "ncta_0":
+        specs = [("axpy", 1, _AXPY), ("axpy", 0, _AXPY), ("axpy", 1, _AXPY)]
+    elif case == "ncta_257":
+        specs = [("axpy", 1, _AXPY), ("axpy", 1, _AXPY), ("axpy", 257 % 65536, _AXPY)]
+    elif case == "emit_task":
+        specs = [("axpy", 1, _AXPY), ("rl_emit", 1, _EMIT), ("axpy", 1, _AXPY)]
+    elif case == "segment_overflow":   # a range whose end passes 2^64
+        specs = [("axpy", 1, _AXPY), ("axpy", 1, {"x": 2**64 - 8, "y": 8192, "n": 16, "a": 1.0}),
+                 ("axpy", 1, _AXPY)]
+    packed = _noalloc_rows(specs)
+    if case == "unknown_op":
+        packed["op"][1] = 77
+    if case == "reserved":
+        packed["reserved"][2] = 1
+    assert acs.acs_run_noalloc(8, ids, packed) == expect
+
+
+def test_noalloc_refuses_bad_window_and_size_on_the_host(lib):
+    import numpy as np
+    packed = _noalloc_rows([("axpy", 1, _AXPY)])
+    ids = np.array([1], np.uint32)
+    assert acs.acs_run_noalloc(0, ids, packed) == acs.ACS_ERR_INVALID
+    assert acs.acs_run_noalloc(65, ids, packed) == acs.ACS_ERR_INVALID
+    n = acs.ACS_NOALLOC_MAX_TASKS + 1
+    big = np.repeat(packed, n)
+    assert acs.acs_run_noalloc(8, np.arange(n, dtype=np.uint32), big) == acs.ACS_ERR_INVALID
+    assert acs.acs_run_noalloc(8, ids[:0], packed[:0]) == acs.ACS_OK    # nothing to run
+
+
+def test_noalloc_valid_tasks_without_a_gpu_fail_cleanly(lib):
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    packed = _noalloc_rows([("axpy", 1, _AXPY)] * 2)
+    assert acs.acs_run_noalloc(8, np.array([1, 2], np.uint32), packed) == acs.ACS_ERR_DEVICE

@@ -187,3 +187,63 @@ def test_tasks_with_many_segments(W):
     assert deps.edges_from_masks([int(m) for m in masks], W) == deps.window_dag(E, W)
     assert not deps.check_legal(E, [int(x) for x in start], [int(x) for x in retire])
     assert sum(1 for rd, wr in segs if len(rd) + len(wr) > 4) > 100
+
+
+def test_emit_task_with_a_zero_cta_count_fails_invalid_and_leaves_the_device_usable():
+    """An emit task copies chunk CTA counts from its table into the tasks it
+    appends; a 0 there would leave a task unrun. The device checks the entries
+    before appending anything: the launch ends with ACS_ERR_INVALID from
+    acs_sync, and a fresh context then runs the same stream to the oracle's
+    result."""
+    p = sg.RLParams(n_env=64, steps=5)
+    sim = sg.RLSim(11, p)
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    n_chunks = p.n_env // p.chunk
+    with harness.Context(32, capacity=1 << 12, timeout_s=2) as ctx:
+        drv = harness.RLEmitDriver(sim, bufs, ctx)      # the host check passes the table ...
+        drv.table[(2 * 2 + 1) * n_chunks + 3] = 0       # ... then step 2's integrate, chunk 3, is spoilt
+        drv.submit()
+        ctx.flush()
+        code = ctx.sync_code()
+        assert code == acs.ACS_ERR_INVALID, acs.acs_strerror(code)
+        assert acs.acs_error(ctx.h) == acs.ACS_ERR_INVALID               # sticky
+    sim = sg.RLSim(11, p)
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    with harness.Context(32, capacity=1 << 12) as ctx:
+        n = harness.RLEmitDriver(sim, bufs, ctx).run()
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(11, sg.RLParams(n_env=64, steps=5)), emit=True)
+    assert n == len(o_tasks)
+    out = bufs.download()
+    for k in ("pos", "vel", "cont", "nisl"):
+        assert np.array_equal(out[k], o_bufs[k]), k
+
+
+def test_host_abort_mid_stream_stops_cleanly_and_leaves_the_device_usable():
+    """acs_abort while a launch runs: elementwise tasks, then a task waiting on
+    a flag nothing sets, then more tasks. The launch ends well before any wait
+    limit, acs_sync returns ACS_ERR_STOPPED (sticky), and a fresh context then
+    runs a stream to the oracle's result."""
+    flag = torch.zeros(4, dtype=torch.int32, device="cuda")
+    s = sg.elementwise_stream(21, n_tasks=24)
+    bufs = harness.DeviceBuffers(s.buffers)
+    ids, packed = harness.pack_tasks(s.tasks, bufs)
+    wait = harness._args_row("wait_flag", 1, {"flag": flag.data_ptr(), "limit_ns": 4_000_000_000})
+    with harness.Context(8, timeout_s=5) as ctx:
+        ctx.submit_packed(ids[:12], packed[:12])
+        ctx.submit_packed(np.array([12], np.uint32), wait)
+        ctx.submit_packed(ids[12:] + np.uint32(1), packed[12:])
+        ctx.flush()
+        time.sleep(0.05)                                  # the launch is blocked on the waiting task
+        t0 = time.time()
+        assert acs.acs_abort(ctx.h) == acs.ACS_OK
+        code = ctx.sync_code()
+        dt = time.time() - t0
+        assert code == acs.ACS_ERR_STOPPED, acs.acs_strerror(code)
+        assert dt < 1.0, dt
+        assert acs.acs_error(ctx.h) == acs.ACS_ERR_STOPPED
+        assert acs.acs_submit(ctx.h, 100, _nop_args(), [], []) == acs.ACS_ERR_STOPPED
+        assert acs.acs_flush(ctx.h) == acs.ACS_ERR_STOPPED
+    s2 = sg.elementwise_stream(22, n_tasks=32)
+    out, _, _ = harness.run_stream(s2)
+    ref = execute.run_inorder(s2.buffers, s2.tasks)
+    assert all(np.array_equal(out[k], ref[k]) for k in ref)

@@ -12,6 +12,8 @@ import torch
 import streamgen as sg
 from oracle import addresses, deps, execute
 
+import fpcheck
+
 pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
@@ -19,7 +21,6 @@ if torch.cuda.is_available():
     build.build()
     from paper_2401_12377_b300 import autotune, harness
 
-DNN_RTOL = 1e-5
 
 
 def _oracle(sp):
@@ -54,8 +55,7 @@ def test_batched_streams_parity(W):
                 if sp.kind == "rl" or o.dtype != np.float32:
                     assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
                 else:
-                    scale = max(float(np.abs(o).max()), 1e-30)
-                    assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+                    fpcheck.assert_per_element({k: g}, {k: o}, f"stream {i}")
         assert n == total
 
 
@@ -77,8 +77,7 @@ def test_batched_host_driven_outputs(mode):
             if sp.kind == "rl":
                 assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
             else:
-                scale = max(float(np.abs(o).max()), 1e-30)
-                assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+                fpcheck.assert_per_element({k: g}, {k: o}, f"stream {i}")
     assert n == total
 
 
@@ -109,8 +108,7 @@ def test_batched_resident_pipelined_submission():
             if sp.kind == "rl" or o.dtype != np.float32:
                 assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
             else:
-                scale = max(float(np.abs(o).max()), 1e-30)
-                assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+                fpcheck.assert_per_element({k: g}, {k: o}, f"stream {i}")
 
 
 def test_batched_repeats_in_one_context():
@@ -183,6 +181,5 @@ def test_batched_full_size_in_the_benchmarked_configuration():
             if sp.kind == "rl" or o.dtype != np.float32:
                 assert np.array_equal(g.view(np.uint8), o.view(np.uint8)), (i, k)
             else:
-                scale = max(float(np.abs(o).max()), 1e-30)
-                assert float(np.abs(g.astype(np.float64) - o).max()) <= DNN_RTOL * scale, (i, k)
+                fpcheck.assert_per_element({k: g}, {k: o}, f"stream {i}")
     assert n == total == 82508

@@ -13,6 +13,8 @@ import torch
 import streamgen as sg
 from oracle import addresses, deps, execute
 
+import fpcheck
+
 pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
@@ -20,7 +22,6 @@ if torch.cuda.is_available():
     build.build()
     from paper_2401_12377_b300 import acs, harness
 
-DNN_RTOL = 1e-5
 
 
 def _check(ctx, stream, first, tasks, buffers, W):
@@ -42,9 +43,7 @@ def _same(g, o):
 
 
 def _close(g, o):
-    for k in o:
-        scale = max(float(np.abs(o[k]).max()), 1e-30)
-        assert float(np.abs(g[k].astype(np.float64) - o[k]).max()) <= DNN_RTOL * scale, k
+    fpcheck.assert_per_element(g, o, "resident")
 
 
 @pytest.mark.parametrize("W", [4, 8, 32])

@@ -9,6 +9,8 @@ import torch
 import streamgen as sg
 from oracle import execute
 
+import fpcheck
+
 pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
@@ -16,7 +18,6 @@ if torch.cuda.is_available():
     build.build()
     from paper_2401_12377_b300 import harness, serving
 
-DNN_RTOL = 1e-5
 
 
 def _oracle(cat, k):
@@ -33,9 +34,8 @@ def _close(g, o, exact):
     for k in o:
         if exact:
             assert np.array_equal(g[k].view(np.uint8), o[k].view(np.uint8)), k
-        else:
-            scale = max(float(np.abs(o[k]).max()), 1e-30)
-            assert float(np.abs(g[k].astype(np.float64) - o[k]).max()) <= DNN_RTOL * scale, k
+    if not exact:
+        fpcheck.assert_per_element(g, o, "served request")
 
 
 @pytest.fixture(scope="module")

@@ -169,6 +169,64 @@ def test_solve_conserves_momentum_of_an_island():
     assert not np.array_equal(b0["vel"], b1["vel"])        # contacts existed
 
 
+@pytest.mark.parametrize("wi,wj", [(1.0, 1.0), (0.5, 2.0)])
+def test_solve_resting_overlap_gets_the_bias_velocity_in_closed_form(wi, wj):
+    """A resting pair that overlaps by more than the slop. The first sweep
+    finds v_n = 0 and applies dl = beta_dt * (pen - slop) / (w_i + w_j); every
+    later sweep then sees v_n equal to the bias and applies nothing. So the
+    result, for any number of sweeps, is v_i = -dl * w_i * n, v_j = +dl * w_j * n
+    and a relative normal velocity of exactly the Baumgarte bias: this pins the
+    bias term's sign, factor and the slop's place in it."""
+    beta_dt, slop = f32(48.0), f32(0.001)
+    b = _solve(_pair_env([0, 0, 0], [0, 0, 0], gap=-0.01, mi=wi, mj=wj), beta_dt=beta_dt, slop=slop)
+    v = b["vel"].reshape(S, 3).astype(np.float64)
+    p = b["pos"].reshape(S, 3).astype(np.float64)
+    dist = p[1, 0] - p[0, 0]
+    pen = 0.2 - dist                                       # radii 0.1 + 0.1
+    assert pen > float(slop)
+    bias = float(beta_dt) * (pen - float(slop))
+    dl = bias / (wi + wj)
+    assert v[0, 0] == pytest.approx(-dl * wi, rel=1e-5)
+    assert v[1, 0] == pytest.approx(dl * wj, rel=1e-5)
+    assert v[1, 0] - v[0, 0] == pytest.approx(bias, rel=1e-5)
+    assert np.all(v[:, 1:] == 0) and np.all(v[2:] == 0)
+    # a pair overlapping by less than the slop gets no bias at all
+    b = _solve(_pair_env([0, 0, 0], [0, 0, 0], gap=-0.0005), beta_dt=beta_dt, slop=slop)
+    assert np.all(b["vel"] == 0)
+
+
+def test_solve_chain_pins_eight_sequential_sweeps():
+    """Three equal spheres in a row touching (contacts (0,1) then (1,2)), no
+    bias (beta_dt = 0), sphere 0 moving at 1 toward the others. One
+    Gauss-Seidel sweep maps (a, b, b) to ((a + b) / 2, (a + 3b) / 4,
+    (a + 3b) / 4), so a - b shrinks by 4 per sweep while a + 2b = 1 (momentum):
+    after s sweeps v0 = (1 + 2 * 4^-s) / 3 and v1 = v2 = (1 - 4^-s) / 3. Every
+    value is a dyadic rational with at most 17 bits (normals are exactly
+    (1, 0, 0)), so fp32 gives them exactly and only s = 8 matches; a Jacobi
+    sweep, a reordered contact list or another sweep count all give other
+    values."""
+    pos = np.tile([[5.0, 5.0, 5.0]], (S, 1)) + np.arange(S)[:, None] * 10.0
+    pos[0] = [1.0, 1.0, 1.0]
+    pos[1] = [1.1875, 1.0, 1.0]
+    pos[2] = [1.375, 1.0, 1.0]
+    radius = np.full(S, 0.125)
+    vel = np.zeros((S, 3)); vel[0, 0] = 1.0
+    b = _bp(_env(pos, radius, np.ones(S), vel))
+    nc, ni, _, _, pairs = _decode(b["cont"])
+    assert pairs == [(0, 1), (1, 2)] and ni == 1
+    out = _solve(_env(pos, radius, np.ones(S), vel), beta_dt=f32(0.0))
+    v = out["vel"].reshape(S, 3)
+    s = 8
+    a = Fraction(1 + 2 * Fraction(1, 4 ** s), 3)
+    bb = Fraction(1 - Fraction(1, 4 ** s), 3)
+    assert a.denominator <= 2 ** 17 and bb.denominator <= 2 ** 17
+    assert Fraction(float(v[0, 0])) == a
+    assert Fraction(float(v[1, 0])) == bb and Fraction(float(v[2, 0])) == bb
+    for other in (7, 9):      # neighbouring sweep counts give different exact values
+        assert Fraction(1 + 2 * Fraction(1, 4 ** other), 3) != a
+    assert np.all(v[:, 1:] == 0) and np.all(v[3:] == 0)
+
+
 def test_solve_without_contacts_is_identity():
     b = _pair_env([1, 0, 0], [-1, 0, 0], gap=0.5)
     out = _solve(b)

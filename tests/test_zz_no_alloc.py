@@ -1,8 +1,9 @@
-"""acs_run_noalloc, the entry point for callers that cannot allocate (e.g.
-while a CUDA graph is being captured, or inside a framework that owns the
-device memory budget): it must give exactly what the regular entry points
-(acs_init / acs_submit_ops / acs_flush / acs_sync) give, on consecutive calls
-that share its fixed scratch array. Collected last on purpose."""
+"""acs_run_noalloc, the entry point for callers that cannot allocate (code
+inside a framework that owns the device memory budget, or a path that cannot
+absorb an allocator's latency or failure): it must give exactly what the
+regular entry points (acs_init / acs_submit_ops / acs_flush / acs_sync) give,
+on consecutive calls that share its fixed scratch array. Collected last on
+purpose."""
 import numpy as np
 import pytest
 import torch
@@ -47,3 +48,19 @@ def test_noalloc_rejects_more_tasks_than_its_scratch_holds():
     packed["ncta"] = 1
     assert acs.acs_run_noalloc(8, ids, packed) == acs.ACS_ERR_INVALID
     assert acs.acs_run_noalloc(0, ids[:1], packed[:1]) == acs.ACS_ERR_INVALID
+
+
+def test_noalloc_at_its_limits_matches_the_oracle():
+    """The largest call the scratch array takes: ACS_NOALLOC_MAX_TASKS tasks,
+    window 64, every task 256 CTAs, so the work ring carries as many units as
+    can ever be in flight. Outputs must equal the oracle's in-order run bit for
+    bit (elementwise bodies round each operation once, like the oracle)."""
+    from oracle import execute
+    s = sg.elementwise_stream(5, n_tasks=acs.ACS_NOALLOC_MAX_TASKS, n_buffers=64, window=64)
+    for t in s.tasks:
+        t.ncta = acs.ACS_MAX_NCTA
+    ref = execute.run_inorder(s.buffers, s.tasks)
+    for call in range(2):
+        out = _noalloc_run(s, 64)
+        for k in ref:
+            assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), (call, k)
