@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tasks/s & step-time speedup vs in-order stream + CUDA graph; p50/p99 latency"
 WORKLOAD = "rigid-sphere RL-sim stream: 256 envs x 32 spheres, 50 steps, window 32, ~300 tasks/step of 1-16 CTAs"
-WORKLOAD_DNN = ("dynamic DNN: gated residual MLP, hidden 256, 24 blocks, shared weights; 100 inputs for each "
+WORKLOAD_DNN = ("dynamic DNN: gated residual MLP, hidden 256, 24 blocks, shared weights; {per_b} inputs for each "
                 "batch size 1, 2, 4, 8, one flush per input, window 32")
 WORKLOAD_STATIC = ("static irregular DAG: randomly wired network, 3 stages x 32 nodes (GEMV 256x256 of 1-8 CTAs, "
                    "bias+ReLU, input aggregation), 411 tasks per input, 100 inputs per step, window 32")
@@ -72,6 +72,10 @@ def parse():
                     help="rlsim: also time windows 8..64, ring and free-slot (span 64)")
     ap.add_argument("--no-baselines", action="store_true", help="skip the in-order / graph arms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="rlsim: skip the compact runs of the other workloads (tiny, dnn, batched, serving)")
+    ap.add_argument("--serving-seconds", type=float, default=2.0,
+                    help="seconds of arrivals in the compact serving run of the default benchmark")
     return ap.parse_args()
 
 
@@ -712,7 +716,8 @@ def per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, 
 
 def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     def make(mode, W, seed, resident):
-        return DNNInputs(torch, mode, W, args.cta_slots, seed, resident=resident)
+        return DNNInputs(torch, mode, W, args.cta_slots, seed, per_b=getattr(args, "dnn_per_b", 100),
+                         resident=resident)
 
     def baselines(line, ms_step, k, W, seed):
         for mode in ("inorder", "graph", "sw"):
@@ -777,8 +782,8 @@ def bench_dnn(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
         return {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
                 "sample": f"first {k} inputs of the step ({n} tasks), single-threaded numpy, {dt:.1f} s"}
 
-    return per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, make, WORKLOAD_DNN, "",
-                           baselines, e2e, oracle)
+    return per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, make,
+                           WORKLOAD_DNN.format(per_b=getattr(args, "dnn_per_b", 100)), "", baselines, e2e, oracle)
 
 
 class StaticInputs:
@@ -892,13 +897,154 @@ def bench_static(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                            "; 24 MB of weights per input", baselines, e2e, oracle)
 
 
+class _ArenaAddr:
+    """pack_task's view of named buffers placed at fixed device addresses."""
+
+    def __init__(self, base):
+        self.base = base
+
+    def ptr(self, ref) -> int:
+        return self.base[ref.buf] + ref.off * 4
+
+
+class TinyStreams:
+    """The tiny elementwise workload: streams of 64 axpy / scale / add tasks
+    over 16 buffers of 4096 floats (window 8), seeds 0 .. n - 1, each its own
+    flush and persistent launch, run back to back. All streams' buffers sit in
+    one device arena (n x 256 KiB: 250 MiB for 1000 streams, larger than L2)."""
+
+    N_BUF, N_ELEM = 16, 4096
+
+    def __init__(self, torch, mode, n=1000, window=8, cta_slots=0):
+        import streamgen as sg
+        from paper_2401_12377_b300 import harness
+        self.torch = torch
+        self.streams = [sg.elementwise_stream(seed) for seed in range(n)]
+        per = self.N_BUF * self.N_ELEM
+        host = np.concatenate([st.buffers[f"b{i}"] for st in self.streams for i in range(self.N_BUF)])
+        self.host_pinned = torch.from_numpy(host).pin_memory()
+        self.arena = self.host_pinned.cuda()
+        self.pristine = self.arena.clone()
+        base = self.arena.data_ptr()
+        self.packed = []
+        for s, st in enumerate(self.streams):
+            at = _ArenaAddr({f"b{i}": base + (s * per + i * self.N_ELEM) * 4 for i in range(self.N_BUF)})
+            self.packed.append(harness.pack_tasks(st.tasks, at))
+        torch.cuda.current_stream().synchronize()
+        self.ctx = harness.Context(window, mode=mode, timing=True, capacity=1 << 12, cta_slots=cta_slots)
+        self.n_tasks = sum(len(st.tasks) for st in self.streams)
+
+    def reset_device(self):
+        self.arena.copy_(self.pristine, non_blocking=True)
+
+    def run_once(self, latencies=None, e2e_out=None):
+        n = 0
+        per = self.N_BUF * self.N_ELEM
+        for s, (ids, rows) in enumerate(self.packed):
+            t0 = time.perf_counter()
+            if e2e_out is not None:      # this stream's buffers in from pinned host memory
+                self.arena[s * per:(s + 1) * per].copy_(self.host_pinned[s * per:(s + 1) * per], non_blocking=True)
+            self.ctx.submit_packed(ids + np.uint32(self.ctx.tail(0)), rows)
+            self.ctx.flush()
+            self.ctx.sync()
+            if e2e_out is not None:      # and its buffers back
+                e2e_out[s * per:(s + 1) * per].copy_(self.arena[s * per:(s + 1) * per], non_blocking=True)
+            if latencies is not None:
+                latencies.append(time.perf_counter() - t0)
+            n += len(ids)
+        return n
+
+
+def bench_tiny(args, torch, dist, world, rank, peaks, peak_src, flush_buf, n_streams=1000):
+    """The tiny elementwise workload (1000 streams, each its own launch) with
+    its in-order and CUDA-graph baselines, end-to-end arm and CPU oracle."""
+    W = 8
+    arm = TinyStreams(torch, "window", n_streams, W, args.cta_slots)
+    lat = []
+    res = time_arm(arm, args.steps, args.warmup, flush_buf, lat)
+    ms_step = statistics.mean(res["ms"])
+    max_ms = max_over_ranks(ms_step, dist, "cuda")
+    tps = res["tasks"] / args.steps
+    st = res["stats"]
+    launches = st["launches"]
+    avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
+    bpl = st["device_seg_bytes"] / max(1, launches)
+    achieved = bpl / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    lus = np.sort(np.array(lat)) * 1e6
+    line = {"value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s", "ms_per_step": max_ms,
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"tiny elementwise streams: {n_streams} streams (seeds 0..{n_streams - 1}) of 64 "
+                                   "FP32 axpy/scale/add tasks over 16 buffers x 4096 floats, 1-4 CTAs per task, "
+                                   "window 8, one flush and one launch per stream, back to back",
+                       "window": W, "streams_per_step": n_streams, "tasks_per_step": tps,
+                       "cta_slots": st.get("cta_slots"),
+                       "l2": "inputs (250 MiB arena) larger than L2, and flushed between timed steps"},
+            "stream_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "acs_persistent_kernel", "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bpl, "avg_launch_us": avg_launch_s * 1e6},
+            "gpu_launches_per_step": launches / args.steps}
+    # end to end: each stream's buffers in from pinned memory and back out
+    out = torch.empty_like(arm.host_pinned).pin_memory()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.current_stream().synchronize()
+    ev0.record()
+    n = arm.run_once(e2e_out=out)
+    ev1.record()
+    torch.cuda.current_stream().synchronize()
+    e_ms = ev0.elapsed_time(ev1)
+    line["e2e"] = {"value": n / (e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": int(arm.host_pinned.numel() * 4 + 320 * n),
+                   "d2h_bytes_per_step": int(out.numel() * 4)}
+    arm.ctx.close()
+    k = max(1, min(args.steps, 3))
+    if not args.no_baselines:
+        for mode in ("inorder", "graph"):
+            b = TinyStreams(torch, mode, n_streams, W, args.cta_slots)
+            r = time_arm(b, k, 1, flush_buf)
+            ms = statistics.mean(r["ms"])
+            kms = r["stats"]["kernel_ms"] / k
+            if mode == "graph":
+                line["graph_with_build"] = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms,
+                                            "host_build_instantiate_ms_per_step":
+                                                (r["stats"]["graph_build_ms"] + r["stats"]["graph_instantiate_ms"]) / k}
+                line["graph_launch"] = {"tasks_per_s": (r["tasks"] / k) / (kms / 1e3), "device_ms_per_step": kms}
+                line["speedup_vs_graph_with_build"] = ms / ms_step
+                line["speedup_vs_graph_launch_only"] = kms / ms_step
+            else:
+                line["inorder"] = {"tasks_per_s": (r["tasks"] / k) / (ms / 1e3), "ms_per_step": ms}
+                line["speedup_vs_inorder"] = ms / ms_step
+            b.ctx.close()
+            del b
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import execute
+        t0 = time.perf_counter()
+        n = i = 0
+        while i < len(arm.streams) and time.perf_counter() - t0 < 5.0:
+            stm = arm.streams[i]
+            execute.run_inorder(stm.buffers, stm.tasks)
+            n += len(stm.tasks)
+            i += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the first {i} streams ({n} tasks), single-threaded numpy, {dt:.1f} s"}
+    else:
+        line["cpu_baseline"] = None
+    return line
+
+
 def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     """64 independent streams of uneven length in one persistent launch, window
     and CTA slots from the autotuner; lockstep host-driven baselines."""
     import streamgen as sg
-    from paper_2401_12377_b300 import autotune, harness
-    seed = 1 + rank
-    specs = sg.batched_specs(seed)
+    from paper_2401_12377_b300 import autotune, harness, shard
+    # one batch for the whole job; with several ranks each runs its share of
+    # the streams (longest first to the least-loaded rank), no data collective
+    seed = 1
+    all_specs = sg.batched_specs(seed)
+    part = shard.partition_by_size([sp.target for sp in all_specs], world, rank)
+    specs = [all_specs[i] for i in part]
     S = len(specs)
     cap = 1 << 13
     wl = harness.BatchedWorkload(specs, None)
@@ -914,8 +1060,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                 return wl.run()
             return run
         t0 = time.perf_counter()
-        tuned = autotune.tune(f"{WORKLOAD_BATCHED}|seed={seed}", make_run, n_streams=S, repeats=5,
-                              capacity=cap)
+        tuned = autotune.tune(f"{WORKLOAD_BATCHED}|seed={seed}|part={rank}/{world}", make_run, n_streams=S,
+                              repeats=5, capacity=cap)
         tuned["tune_s"] = time.perf_counter() - t0
         W, slots = tuned["window"], tuned["cta_slots"]
     # the kernel alone: one flush and one launch per pass (roofline from its launches)
@@ -953,15 +1099,16 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
     ms_step = statistics.mean(res["ms"])
     tasks_per_step = res["tasks"] / args.steps
     max_ms = max_over_ranks(ms_step, dist, "cuda")
+    job_tasks_per_step = shard.gather_sum(dist, tasks_per_step)
     st = res1["stats"]
     launches = st["launches"]
     avg_launch_s = (st["kernel_ms"] / 1e3) / max(1, launches)
     bytes_per_launch = st["device_seg_bytes"] / max(1, launches)
     achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6400.0))
-    line = {"metric": METRIC, "value": whole_job_rate(world, tasks_per_step, max_ms / 1e3), "unit": "tasks/s",
+    line = {"metric": METRIC, "value": job_tasks_per_step / (max_ms / 1e3), "unit": "tasks/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "critical_path": {"us": cps[cp_i][0], "tasks_on_chain": cps[cp_i][1], "stream": cp_i,
                               "kernel_us_per_pass": avg_launch_s * 1e6,
@@ -974,7 +1121,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                        "mode": "window scheduler, one resident persistent launch for all streams; each "
                                "stream published as soon as it is submitted",
                        "l2": "not flushed between passes: inputs larger than L2 (384 MB of gated-MLP weights)",
-                       "parallelism": f"independent batches x{world}" if world > 1 else "one GPU"},
+                       "parallelism": (f"one batch split over {world} GPUs by size ({S} of {len(all_specs)} "
+                                       f"streams on rank 0)") if world > 1 else "one GPU"},
             "autotune": None if tuned is None else {
                 "window": W, "cta_slots": slots, "tune_s": tuned.get("tune_s"), "cached": tuned.get("cached", False),
                 "table": [(r["window"], r["cta_slots"], round(r["ms"], 4)) for r in tuned.get("table", [])]},
@@ -1057,8 +1205,10 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
     by the host minus arrival; every request's inputs go host to device and its
     results device to host inside the run."""
     import streamgen as sg
-    from paper_2401_12377_b300 import harness, serving
-    seed = 1 + rank
+    from paper_2401_12377_b300 import harness, serving, shard
+    # one arrival process for the whole job; with several ranks, request i is
+    # served by rank i mod world (each rank sees a Poisson process of rate / world)
+    seed = 1
     t_prep = time.perf_counter()
     specs = sg.serving_catalogue(seed)
     cat = serving.Catalogue(specs)
@@ -1066,7 +1216,9 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
     W = args.window or 32
     n_req = int(round(args.rate * args.steps))
     arrivals, kinds = sg.poisson_arrivals(seed, n_req, args.rate, len(specs))
-    wa, wk = sg.poisson_arrivals(seed + 1000, max(1, 100 * args.warmup), args.rate, len(specs))
+    mine = shard.partition_round_robin(n_req, world, rank)
+    arrivals, kinds = arrivals[mine], kinds[mine]
+    wa, wk = sg.poisson_arrivals(seed + 1000, max(1, 100 * args.warmup), args.rate / world, len(specs))
     ctx = harness.Context(W, n_streams=args.slots, resident=True, timing=True, capacity=1 << 13)
     srv = serving.Server(cat, ctx, budget_bytes=20 << 30, readback=True)
     srv.run(wa, wk)
@@ -1078,28 +1230,52 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
     ctx.stop()
     st = ctx.stats()
     ctx.close()
-    lat = np.sort(r["latency_s"]) * 1e3
-    q = np.sort(r["queue_s"]) * 1e3
-    tasks = int(r["tasks"].sum())
-    span = r["span_s"]
-    tps = r["tasks_per_s"]
-    span = max_over_ranks(span, dist, "cuda")
-    value = whole_job_rate(world, tasks, span)
+    # every rank's per-request logs gathered on rank 0 (the only collective)
+    lat = np.sort(shard.gather_values(dist, r["latency_s"], rank, world)) * 1e3
+    q = np.sort(shard.gather_values(dist, r["queue_s"], rank, world)) * 1e3
+    tasks = int(shard.gather_sum(dist, float(r["tasks"].sum())))
+    span = max_over_ranks(r["span_s"], dist, "cuda")
+    value = tasks / span
     pct = lambda a, p: float(a[min(len(a) - 1, int(p * len(a)))])
     mean_len = float(np.mean([specs[int(k)].target for k in kinds]))
     kernel_s = st["kernel_ms"] / 1e3
+    # where the tail comes from: queueing (admission waits) or service, per
+    # request kind and length
+    lat_ms, q_ms = r["latency_s"] * 1e3, r["queue_s"] * 1e3
+    svc_ms = lat_ms - q_ms
+    kind_of = np.array([specs[int(k)].kind for k in kinds])
+    length = np.array([specs[int(k)].target for k in kinds])
+
+    def dist_of(a):
+        a = np.sort(a)
+        return {"n": int(len(a)), "p50": pct(a, 0.5), "p99": pct(a, 0.99)} if len(a) else None
+
+    slow = lat_ms >= np.quantile(lat_ms, 0.99) if len(lat_ms) else np.zeros(0, bool)
+    breakdown = {
+        "service_ms": dist_of(svc_ms),
+        "by_kind": {k: {"latency_ms": dist_of(lat_ms[kind_of == k]), "service_ms": dist_of(svc_ms[kind_of == k]),
+                        "queue_ms": dist_of(q_ms[kind_of == k])} for k in ("rl", "dnn")},
+        "by_length": {f"{lo}-{hi}": {"latency_ms": dist_of(lat_ms[(length >= lo) & (length < hi)]),
+                                     "service_ms": dist_of(svc_ms[(length >= lo) & (length < hi)])}
+                      for lo, hi in ((100, 300), (300, 1000), (1000, 2500), (2500, 5001))},
+        "slowest_1pct": {"n": int(slow.sum()), "rl_share": float(np.mean(kind_of[slow] == "rl")) if slow.any() else None,
+                         "mean_tasks": float(length[slow].mean()) if slow.any() else None,
+                         "mean_queue_ms": float(q_ms[slow].mean()) if slow.any() else None,
+                         "mean_service_ms": float(svc_ms[slow].mean()) if slow.any() else None}}
     line = {"metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_SERVING, "requests": n_req, "rate_per_s": args.rate,
                        "step": "one second of arrivals", "slots": args.slots, "window": W, "budget_gb": 20,
                        "catalogue_types": len(specs), "mean_request_tasks": mean_len,
                        "timing": "host clock (perf_counter) from first arrival to last completion",
                        "l2": "not flushed: a continuous open-loop run over > 126 MB of request data",
-                       "parallelism": f"independent servers x{world}" if world > 1 else "one GPU"},
+                       "parallelism": (f"one arrival process split over {world} GPUs round-robin, latency logs "
+                                       f"gathered on rank 0") if world > 1 else "one GPU"},
             "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": float(lat.mean()),
                            "max": float(lat[-1])},
             "queue_wait_ms": {"p50": pct(q, 0.5), "p99": pct(q, 0.99)},
+            "latency_breakdown": breakdown,
             "offered_tasks_per_s": args.rate * mean_len,
             "mean_in_flight": r["mean_in_flight"], "peak_device_bytes": r["peak_bytes"],
             "requests_per_s": n_req / span,
@@ -1124,6 +1300,41 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
     elif rank == 0:
         line["cpu_baseline"] = None
     return line
+
+
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "stream_latency_us", "input_latency_us",
+            "latency_ms", "queue_wait_ms", "latency_breakdown", "offered_tasks_per_s", "requests_per_s",
+            "mean_in_flight", "roofline", "critical_path", "cpu_baseline", "e2e", "speedup_vs_inorder",
+            "speedup_vs_graph_with_build", "speedup_vs_graph_launch_only", "speedup_vs_sw_host_scheduler",
+            "inorder", "graph_with_build", "graph_launch", "sw_host_scheduler", "single_flush", "autotune",
+            "resident_per_input", "gpu_launches", "gpu_launches_per_step", "clocks")
+
+
+def other_configs(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
+    """Compact runs of the tiny, dynamic-DNN, batched and serving workloads,
+    each timed on its own (3 warm-up + 3 timed steps; dnn 25 inputs per batch
+    size; serving --serving-seconds of arrivals), with its own baselines,
+    roofline, end-to-end arm and CPU oracle sample."""
+    import argparse as _ap
+    out = {}
+    base = dict(vars(args), window=0, cta_slots=0, no_tune=False, steps=3, warmup=3)
+    t0 = time.perf_counter()
+    out["tiny"] = bench_tiny(_ap.Namespace(**base), torch, dist, world, rank, peaks, peak_src, flush_buf)
+    out["tiny"]["bench_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    d = bench_dnn(_ap.Namespace(**dict(base, dnn_per_b=25)), torch, dist, world, rank, peaks, peak_src, flush_buf)
+    out["dnn"] = {k: d[k] for k in SUB_KEYS if k in d}
+    out["dnn"]["bench_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = bench_batched(_ap.Namespace(**base), torch, dist, world, rank, peaks, peak_src, flush_buf)
+    out["batched"] = {k: b[k] for k in SUB_KEYS if k in b}
+    out["batched"]["bench_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sv = bench_serving(_ap.Namespace(**dict(base, steps=args.serving_seconds, warmup=1)), torch, dist, world,
+                       rank, peaks, peak_src)
+    out["serving"] = {k: sv[k] for k in SUB_KEYS if k in sv}
+    out["serving"]["bench_s"] = time.perf_counter() - t0
+    return out
 
 
 def main():
@@ -1307,6 +1518,10 @@ def main():
         line["cpu_baseline"] = cpu_oracle_rate()
     elif rank == 0:
         line["cpu_baseline"] = None
+
+    # ---- the other workloads, compact, after the headline's timed region -------------------
+    if not args.headline_only:
+        line["configs"] = other_configs(args, torch, dist, world, rank, peaks, peak_src, flush_buf)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
