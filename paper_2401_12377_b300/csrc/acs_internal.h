@@ -77,7 +77,9 @@ __host__ __device__ inline void fold_reads(TaskRec &r) {
 // distinct banks.
 struct alignas(16) HistRec {
     TaskRec r;
-    uint4 pad;
+    uint32_t hi;        // the upper 32 address bits of every segment, when `narrow`
+    uint32_t narrow;    // 1: at most 4 segments, each inside the 4 GiB window [hi << 32, (hi + 1) << 32)
+    uint32_t pad[2];
 };
 static_assert(sizeof(HistRec) == 336, "HistRec layout");
 

@@ -190,15 +190,33 @@ constexpr int kRegSegs = 4;
 struct NewTask {
     Seg a[kRegSegs];
     uint32_t n, w;
+    uint32_t hi, narrow;   // as HistRec
 };
 
-__device__ __forceinline__ NewTask load_new_task(const TaskRec &rj) {
+__device__ __forceinline__ NewTask load_new_task(const HistRec &hj) {
+    const TaskRec &rj = hj.r;
     NewTask t;
     t.n = min((uint32_t)rj.nseg, (uint32_t)kMaxSegs);
     t.w = rj.wmask;
+    t.hi = hj.hi;
+    t.narrow = hj.narrow;
 #pragma unroll
     for (int x = 0; x < kRegSegs; ++x) t.a[x] = x < (int)t.n ? rj.seg[x] : Seg{0, 0};   // unused beyond n
     return t;
+}
+
+// Whether every segment of a record lies in one 4 GiB-aligned window (and
+// there are at most kRegSegs of them): then overlap tests against another such
+// record in the same window compare the low 32 bits only, which decide them
+// exactly. Computed once per record by the loader.
+__device__ __forceinline__ void set_narrow(HistRec &h) {
+    const uint32_t n = min((uint32_t)h.r.nseg, (uint32_t)kMaxSegs);
+    const uint32_t hi = n ? (uint32_t)(h.r.seg[0].start >> 32) : 0u;
+    bool ok = n <= (uint32_t)kRegSegs;
+    for (uint32_t k = 0; k < n && ok; ++k)
+        ok = (uint32_t)(h.r.seg[k].start >> 32) == hi && (uint32_t)(h.r.seg[k].last >> 32) == hi;
+    h.hi = hi;
+    h.narrow = ok ? 1u : 0u;
 }
 
 // Every segment pair of a candidate (ri) and the new task (t, all segments
@@ -218,21 +236,40 @@ __device__ __noinline__ bool rec_conflict_all(const TaskRec &ri, const TaskRec &
 }
 
 // The candidate's first kRegSegs segments are loaded together and every pair
-// with the new task's registers is tested (predicated, no early exit).
-__device__ __forceinline__ bool rec_conflict(const TaskRec &ri, const NewTask &t, const TaskRec &rj) {
+// with the new task's registers is tested (predicated, no early exit): on the
+// low 32 address bits when both records lie in the same 4 GiB window, else on
+// the full 64 bits.
+__device__ __forceinline__ bool rec_conflict(const HistRec &hi_, const NewTask &t, const TaskRec &rj) {
+    const TaskRec &ri = hi_.r;
     const uint32_t ni = min((uint32_t)ri.nseg, (uint32_t)kMaxSegs);
     const uint32_t wi = ri.wmask;
     Seg b[kRegSegs];
 #pragma unroll
     for (int y = 0; y < kRegSegs; ++y) b[y] = ri.seg[y];    // unused entries are masked below
     bool hit = false;
+    if (t.narrow && hi_.narrow && hi_.hi == t.hi) {
+        bool hx[kRegSegs];
 #pragma unroll
-    for (int y = 0; y < kRegSegs; ++y) {
-        const bool yv = (uint32_t)y < ni, yw = (wi >> y) & 1u;
+        for (int x = 0; x < kRegSegs; ++x) {
+            const uint32_t as = (uint32_t)t.a[x].start, al = (uint32_t)t.a[x].last;
+            const bool xw = (t.w >> x) & 1u;
+            bool h = false;
 #pragma unroll
-        for (int x = 0; x < kRegSegs; ++x)
-            hit |= yv && (uint32_t)x < t.n && (yw || ((t.w >> x) & 1u)) && t.a[x].start <= b[y].last &&
-                   b[y].start <= t.a[x].last;
+            for (int y = 0; y < kRegSegs; ++y)
+                h |= (uint32_t)y < ni && (xw || ((wi >> y) & 1u)) && as <= (uint32_t)b[y].last &&
+                     (uint32_t)b[y].start <= al;
+            hx[x] = (uint32_t)x < t.n && h;
+        }
+        hit = (hx[0] || hx[1]) || (hx[2] || hx[3]);
+    } else {
+#pragma unroll
+        for (int y = 0; y < kRegSegs; ++y) {
+            const bool yv = (uint32_t)y < ni, yw = (wi >> y) & 1u;
+#pragma unroll
+            for (int x = 0; x < kRegSegs; ++x)
+                hit |= yv && (uint32_t)x < t.n && (yw || ((t.w >> x) & 1u)) && t.a[x].start <= b[y].last &&
+                       b[y].start <= t.a[x].last;
+        }
     }
     if (!hit && (ni > (uint32_t)kRegSegs || t.n > (uint32_t)kRegSegs)) hit = rec_conflict_all(ri, rj);
     return hit;
@@ -372,6 +409,8 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                     reinterpret_cast<uint4 *>(&S.hist[(load_upto + rec) & HM])[part] = __ldcg(src + i);
                 }
                 __syncwarp();
+                if (lane < bhi - load_upto) set_narrow(S.hist[(load_upto + lane) & HM]);
+                __syncwarp();
                 __threadfence_block();
                 load_upto = bhi;
                 if (lane == 0) sts_volatile(&S.sh->complete_upto, load_upto);
@@ -493,9 +532,9 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         }
         bool c0 = false, c1 = false;
         const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
-        const NewTask nt = load_new_task(rj);
-        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM].r, nt, rj);
-        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM].r, nt, rj);
+        const NewTask nt = load_new_task(S.hist[j & HM]);
+        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM], nt, rj);
+        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM], nt, rj);
         // candidate at distance d sits in slot (j - d) mod W; each lane sets
         // the bits of its conflicting candidates, two OR reductions merge them
         const uint32_t js = j % W;
@@ -964,10 +1003,12 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
 
 struct EmitSmem {
     acs_rl_emit_cfg cfg;
-    uint32_t base, n_solve, ok, pad;
+    uint32_t base, ok, pad[2];
     int wcnt[kBlock / 32];
     uint16_t env[1024];        // environments with islands, ascending
-    uint8_t nisl[1024];
+    uint8_t nisl[1024];        // their island counts
+    uint8_t tab_int[1024];     // CTA counts of this step's integrate tasks, by chunk
+    uint8_t tab_bp[1024];      // CTA counts of the next step's broadphase tasks, by chunk
 };
 
 static_assert(sizeof(EmitSmem) <= kBodySmem, "emit smem");
@@ -1001,7 +1042,10 @@ __device__ __forceinline__ Seg seg_of(uint64_t a, uint64_t n) { return Seg{a, a 
 
 // The emit task of step t (one CTA): appends solves, integrates, the next
 // broadphase and the next emit task after the current end of its stream, then
-// publishes the new end with release semantics.
+// publishes the new end with release semantics. Every global read it needs
+// (the cfg block, the island counts, the chunk CTA counts, the stream's end
+// and oldest unreleased task) is issued at once, so the task costs one memory
+// round trip before it writes.
 __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &hdr, uint8_t *smem) {
     EmitSmem &E = *reinterpret_cast<EmitSmem *>(smem);
     const acs_rl_emit_args a = load_args<acs_rl_emit_args>(hdr.args);
@@ -1009,22 +1053,54 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     const uint32_t C = 1u << P.cap_log2, W = P.window;
     StreamCtl *sc = &P.sctl[stream];
     TaskRec *ring = P.recs + (size_t)stream * C;
-    const uint32_t n_env = a.n_env, chunk = a.chunk, n_chunks = a.n_env / a.chunk;
+    const uint32_t n_env = a.n_env, chunk = a.chunk;
+    if (!(n_env <= 1024 && chunk > 0 && n_env % chunk == 0)) {   // self-check of the args (uniform)
+        if (tid == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteEmit);
+        return;
+    }
+    const uint32_t n_chunks = n_env / chunk;
     const bool more = a.step + 1 < a.steps;
-    if (tid < sizeof(acs_rl_emit_cfg) / 4)
-        reinterpret_cast<uint32_t *>(&E.cfg)[tid] = reinterpret_cast<const uint32_t *>(a.cfg)[tid];
-    if (tid == 0) E.ok = n_env <= 1024 && chunk > 0 && n_env % chunk == 0;
-    __syncthreads();
-    if (!E.ok) {
+    constexpr int kPer = 1024 / kBlock;            // environments (and chunks) per thread, at most
+    const uint32_t *nisl_g = reinterpret_cast<const uint32_t *>(a.nisl);
+    const uint8_t *table = reinterpret_cast<const uint8_t *>(a.ncta_table);
+    uint32_t cfgw = 0, base = 0, head = 0, isl[kPer];
+    uint8_t ti[kPer], tb[kPer];
+    if (tid < sizeof(acs_rl_emit_cfg) / 4) cfgw = reinterpret_cast<const uint32_t *>(a.cfg)[tid];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const uint32_t e = tid + r * kBlock;
+        isl[r] = e < n_env ? nisl_g[e] : 0u;
+        ti[r] = e < n_chunks ? table[(a.step * 2 + 1) * n_chunks + e] : (uint8_t)1;
+        tb[r] = more && e < n_chunks ? table[((a.step + 1) * 2 + 0) * n_chunks + e] : (uint8_t)1;
+    }
+    if (tid == 0) {
+        base = ld_relaxed_u32(&sc->end);
+        head = ld_relaxed_u32(&sc->head_pub);
+    }
+    if (tid < sizeof(acs_rl_emit_cfg) / 4) reinterpret_cast<uint32_t *>(&E.cfg)[tid] = cfgw;
+    // the chunk CTA counts this task copies from the table must be 1 .. 255 (a
+    // 0 would leave its task unrun): checked before anything is appended
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const uint32_t c = tid + r * kBlock;
+        if (c < n_chunks) {
+            E.tab_int[c] = ti[r];
+            E.tab_bp[c] = tb[r];
+            bad |= ti[r] == 0 || tb[r] == 0;
+        }
+    }
+    if (__syncthreads_or(bad)) {
         if (tid == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteEmit);
         return;
     }
     // environments with islands, in ascending order (ballot scan per 256)
-    const uint32_t *nisl = reinterpret_cast<const uint32_t *>(a.nisl);
     uint32_t count = 0;
-    for (uint32_t e0 = 0; e0 < n_env; e0 += kBlock) {
-        const uint32_t e = e0 + tid;
-        const uint32_t k = e < n_env ? nisl[e] : 0u;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        if ((uint32_t)r * kBlock >= n_env) break;     // uniform
+        const uint32_t e = r * kBlock + tid;
+        const uint32_t k = isl[r];
         const bool has = k > 0;
         const uint32_t bal = __ballot_sync(0xffffffffu, has);
         if (lane == 0) E.wcnt[warp] = __popc(bal);
@@ -1041,27 +1117,12 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     }
     const uint32_t n_solve = count;
     const uint32_t n_new = n_solve + n_chunks + (more ? n_chunks + 1 : 0);
-    // the chunk CTA counts this task copies from the table must be 1 .. 255 (a
-    // 0 would leave its task unrun): checked before anything is appended
-    const uint8_t *table = reinterpret_cast<const uint8_t *>(a.ncta_table);
-    {
-        bool bad = false;
-        for (uint32_t c = tid; c < n_chunks; c += kBlock) {
-            bad |= table[(a.step * 2 + 1) * n_chunks + c] == 0;
-            if (more) bad |= table[((a.step + 1) * 2 + 0) * n_chunks + c] == 0;
-        }
-        if (__syncthreads_or(bad)) {
-            if (tid == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteEmit);
-            return;
-        }
-    }
-    // position of the first new task; wait (bounded) until the ring positions
-    // it overwrites hold only released tasks no window still looks at
+    // the ring positions the new tasks overwrite must hold only released
+    // tasks no window still looks at: wait (bounded) while they do not
     if (tid == 0) {
-        const uint32_t base = ld_relaxed_u32(&sc->end);
         unsigned long long tw = 0;
         uint32_t ok = 1;
-        while ((int32_t)(base + n_new + W - (ld_relaxed_u32(&sc->head_pub) + C)) > 0) {
+        while ((int32_t)(base + n_new + W - (head + C)) > 0) {
             if (stopped(P)) { ok = 0; break; }
             const unsigned long long now = globaltimer_ns();
             if (tw == 0) tw = now;
@@ -1071,13 +1132,14 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
                 break;
             }
             __nanosleep(256);
+            head = ld_relaxed_u32(&sc->head_pub);
         }
         E.base = base;
         E.ok = ok;
     }
     __syncthreads();
     if (!E.ok) return;
-    const uint32_t base = E.base;
+    base = E.base;
     const acs_rl_emit_cfg &cfg = E.cfg;
     constexpr uint64_t kPos = 32 * 3 * 4, kProp = 32 * 2 * 4, kRec = ACS_RL_REC_BYTES;
     for (uint32_t k = tid; k < n_new; k += kBlock) {
@@ -1100,16 +1162,14 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             // reads prop, reads and writes pos and vel (the host's folded order)
             sg[0] = seg_of(x.prop, chunk * kProp);
             sg[1] = seg_of(x.pos, chunk * kPos); sg[2] = seg_of(x.vel, chunk * kPos);
-            const uint16_t nc = table[(a.step * 2 + 1) * n_chunks + c];
-            put_rec(r, seq, ACS_OP_RL_INTEGRATE, nc, &x, sizeof x, sg, 3, 6u, 6u);
+            put_rec(r, seq, ACS_OP_RL_INTEGRATE, E.tab_int[c], &x, sizeof x, sg, 3, 6u, 6u);
         } else if (k < n_solve + 2 * n_chunks) {
             const uint64_t c = k - n_solve - n_chunks, e0 = c * chunk;
             acs_rl_broadphase_args x{cfg.pos + e0 * kPos, cfg.prop + e0 * kProp, cfg.cont + e0 * kRec,
                                      a.nisl + e0 * 4, chunk, 0};
             sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.prop, chunk * kProp);
             sg[2] = seg_of(x.cont, chunk * kRec); sg[3] = seg_of(x.nisl, chunk * 4);
-            const uint16_t nc = table[((a.step + 1) * 2 + 0) * n_chunks + c];
-            put_rec(r, seq, ACS_OP_RL_BROADPHASE, nc, &x, sizeof x, sg, 4, (1u << 2) | (1u << 3), 0u);
+            put_rec(r, seq, ACS_OP_RL_BROADPHASE, E.tab_bp[c], &x, sizeof x, sg, 4, (1u << 2) | (1u << 3), 0u);
         } else {
             acs_rl_emit_args x = a;
             x.step = a.step + 1;
