@@ -182,11 +182,11 @@ struct alignas(128) Mirror {
     unsigned long long heartbeat;
 };
 
-// What a worker needs beside its cell's payload, written once per task at
-// insertion and indexed like the descriptor ring: the upstream slots it must
-// still wait for (bit b: the task in window slot b) and the task's seq. Task
-// q + capacity reuses the entry only after task q retired, and every CTA of q
-// reads it before q can retire.
+// What a worker needs beside its cell's payload, written once per task by the
+// checker warp and indexed like the descriptor ring: the conflicting
+// candidates it must wait for (bit b: the task in window slot b) and the
+// task's seq. Task q + capacity reuses the entry only after task q retired,
+// and every CTA of q reads it before q can retire.
 struct alignas(16) TaskAux {
     unsigned long long up;
     uint32_t seq;
@@ -199,9 +199,9 @@ struct KParams {
     unsigned long long *cells;// work ring: low 32 bits sequence, high 32 payload
                               // (descriptor index << 8 | CTA index)
     TaskAux *taskaux;         // [n_streams][capacity], like recs
-    // [n_streams][kMaxWindow] done words: (seq + 1) << 32 | CTAs not yet
-    // finished, of the slot's latest task (set when it is published; each CTA
-    // subtracts one with release semantics)
+    // [n_streams][capacity] done words, indexed like recs: (seq + 1) << 32 |
+    // CTAs not yet finished, of the position's latest task (set when the loader
+    // takes the task; each CTA subtracts one with release semantics)
     unsigned long long *done;
     unsigned long long *log_mask, *log_start, *log_retire;   // [n_streams][log_capacity]
     SchedStats *sched_stats;  // [n_streams]
@@ -236,7 +236,6 @@ __host__ __device__ inline uint32_t hist_size(uint32_t window) { return window <
 // mask still to wait for.
 constexpr uint32_t kPubSlots = 4;
 struct PubBatch {
-    unsigned long long up[32];
     uint32_t q[32], off[32], n[32];
     uint32_t nins, p0, total, pad;
 };
@@ -247,7 +246,7 @@ struct PubQueue {
 
 inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t H = hist_size(window);
-    const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + kMaxWindow * 4 * 2;
+    const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + kMaxWindow * 4 * 2;   // hist, pmask, ptag, sh, expect, slotpos
     return (base + 15u) / 16u * 16u + (uint32_t)sizeof(PubQueue);
 }
 

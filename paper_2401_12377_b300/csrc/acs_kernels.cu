@@ -10,16 +10,19 @@
 //   warps 1..4 run the segment-overlap test of Alg. 1 (extended to
 //          read-after-write) of each task against its W - 1 predecessors,
 //          one predecessor per lane; a ballot turns the per-lane results into
-//          the task's upstream-candidate mask;
-//   warp 5 publishes the pending insertion batches to the work ring (aux
-//          words, one fence per pass, the cells' sequence words);
-//   warp 6 polls the done words of executing slots (acquire loads);
+//          the task's upstream-candidate mask, which goes to the task's aux
+//          word (what its worker CTAs wait for);
+//   warp 5 publishes the pending insertion batches to the work ring (one
+//          fence per pass, then the cells' sequence words);
+//   warp 6 polls the done words of executing tasks (acquire loads);
 //   warp 7 streams descriptors into a shared-memory history ring ahead of
-//          use (and, in a resident launch, follows the host-published ends).
+//          use, setting each new task's done word (and, in a resident launch,
+//          follows the host-published ends).
 //
 // CTAs [n_streams, grid) are workers: each claims work-ring positions one at a
 // time, runs the body for one (task, CTA index) unit, then takes itself off
-// its slot's done word (seq + 1, CTAs still running) with a release reduction.
+// its task's done word (seq + 1, CTAs still running; one per descriptor ring
+// position) with a release reduction.
 //
 // Every wait is bounded by timeout_ns of no progress (a resident launch's
 // waits for the host by its idle limit); on expiry the waiter records
@@ -71,8 +74,8 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 // A done word shows task `want - 1` (want = seq + 1) complete when it names
-// that task with no CTA left, or names a later task of the slot (which the
-// slot takes only after the earlier one retired).
+// that task with no CTA left, or names a later task of the same ring position
+// (which the position takes only after the earlier task retired).
 __device__ __forceinline__ bool slot_done(unsigned long long w, uint32_t want) {
     const uint32_t hi = (uint32_t)(w >> 32);
     return (int32_t)(hi - want) > 0 || (hi == want && (uint32_t)w == 0u);
@@ -142,7 +145,8 @@ struct SchedShared {
     uint32_t end;            // stream end known to the CTA (grows while the stream is open)
     uint32_t head_pos;       // sole producer: work-ring position of the oldest unreleased task's
                              // first unit (every unit below it belongs to a retired task)
-    uint32_t pad[3];
+    uint32_t released;       // every task below it retired (the window's release point)
+    uint32_t pad[2];
 };
 static_assert(sizeof(SchedShared) == 32, "SchedShared size (sched_smem_bytes)");
 
@@ -409,7 +413,19 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                     reinterpret_cast<uint4 *>(&S.hist[(load_upto + rec) & HM])[part] = __ldcg(src + i);
                 }
                 __syncwarp();
-                if (lane < bhi - load_upto) set_narrow(S.hist[(load_upto + lane) & HM]);
+                if (lane < bhi - load_upto) {
+                    HistRec &h = S.hist[(load_upto + lane) & HM];
+                    set_narrow(h);
+                    // the task's done word: (seq + 1, all its CTAs to go). The
+                    // ring position's previous task (seq - capacity) retired
+                    // before this descriptor was written, so waiters of it read
+                    // the new word as complete, as they must. Tasks below `first`
+                    // belong to earlier launches and have retired: untouched.
+                    const uint32_t q = load_upto + lane;
+                    if ((int32_t)(q - first) >= 0)
+                        st_relaxed_u64(&P.done[((size_t)stream << P.cap_log2) | (q & (C - 1))],
+                                       ((unsigned long long)(q + 1u) << 32) | h.r.ncta);
+                }
                 __syncwarp();
                 __threadfence_block();
                 load_upto = bhi;
@@ -440,8 +456,8 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     }
 }
 
-// Warp 6: polls the done word of every executing slot (acquire loads) and
-// clears the slot's expect word once its task completed; those acquires, with
+// Warp 6: polls the done word of every executing slot's task (acquire loads)
+// and clears the slot's expect word once its task completed; those acquires, with
 // the publisher's fence before it publishes work, order the retired tasks'
 // writes before every dependent's start. Warp 0 never waits on global memory
 // to retire tasks.
@@ -449,7 +465,8 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t W = P.window;
     SchedSmem S = carve(smem_raw, W);
-    const unsigned long long *done = P.done + stream * kMaxWindow;
+    const uint32_t CM = (1u << P.cap_log2) - 1u;
+    const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
     uint32_t backoff = 32;
     while (!lds_volatile(&S.sh->quit)) {
         const uint32_t e0 = lane < W ? lds_volatile(&S.expect[lane]) : 0u;
@@ -457,8 +474,8 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
         bool h0 = false, h1 = false;
         // acquire loads: a done word read at its task's value orders the
         // task's writes before what this lane does next
-        if (e0) h0 = slot_done(ld_acquire_u64(&done[lane]), e0);
-        if (e1) h1 = slot_done(ld_acquire_u64(&done[lane + 32]), e1);
+        if (e0) h0 = slot_done(ld_acquire_u64(&done[(e0 - 1u) & CM]), e0);
+        if (e1) h1 = slot_done(ld_acquire_u64(&done[(e1 - 1u) & CM]), e1);
         const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
         if (b0 | b1) {
             // release at CTA scope: warp 0 retires a slot once it reads 0 here
@@ -488,6 +505,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     unsigned long long tw = 0;
     unsigned long long seg_bytes = 0, check_cycles = 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
+    const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     for (uint32_t j = first + w; open || j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
         uint32_t spins = 0, backoff = 32;
@@ -533,8 +551,17 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         bool c0 = false, c1 = false;
         const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
         const NewTask nt = load_new_task(S.hist[j & HM]);
-        if (d0 <= W - 1 && d0 <= j) c0 = rec_conflict(S.hist[(j - d0) & HM], nt, rj);
-        if (d1 <= W - 1 && d1 <= j) c1 = rec_conflict(S.hist[(j - d1) & HM], nt, rj);
+        // Without a log, a candidate that already retired is not tested: its
+        // done word reads as complete to the task's workers anyway, and the
+        // publisher's fence orders its writes before this task's units, as for
+        // every conflict farther back than the window. (A stale release point
+        // only means more tests.) With a log, every candidate is tested: the
+        // log holds the window DAG.
+        const uint32_t rel = logging ? 0u : lds_volatile(&S.sh->released);
+        if (d0 <= W - 1 && d0 <= j && (int32_t)(j - d0 - rel) >= 0)
+            c0 = rec_conflict(S.hist[(j - d0) & HM], nt, rj);
+        if (d1 <= W - 1 && d1 <= j && (int32_t)(j - d1 - rel) >= 0)
+            c1 = rec_conflict(S.hist[(j - d1) & HM], nt, rj);
         // candidate at distance d sits in slot (j - d) mod W; each lane sets
         // the bits of its conflicting candidates, two OR reductions merge them
         const uint32_t js = j % W;
@@ -550,7 +577,13 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         mlo = __reduce_or_sync(0xffffffffu, mlo);
         mhi = __reduce_or_sync(0xffffffffu, mhi);
         if (lane == 0) {
-            S.pmask[j & HM] = (unsigned long long)mlo | ((unsigned long long)mhi << 32);
+            const unsigned long long m = (unsigned long long)mlo | ((unsigned long long)mhi << 32);
+            S.pmask[j & HM] = m;
+            // what the task's worker CTAs wait for: every conflicting candidate
+            // (one that has retired by then reads as complete); published to them
+            // by the publisher's fence after the task's insertion
+            *reinterpret_cast<uint4 *>(&P.taskaux[((size_t)stream << P.cap_log2) | (j & ((1u << P.cap_log2) - 1u))]) =
+                make_uint4(mlo, mhi, j, 0u);
             __threadfence_block();
             sts_volatile(&S.ptag[j & HM], j + 1u);
             if (tracing) check_cycles += clock64() - tc0;
@@ -577,6 +610,7 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->quit = 0;
         S.sh->end = P.end[stream];
         S.sh->head_pos = 0;
+        S.sh->released = first;
         if (P.open[stream] || P.resident) {   // published before any emitter of this launch can run
             StreamCtl *sc = &P.sctl[stream];
             sc->end = P.end[stream];
@@ -588,11 +622,11 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
 }
 
 // Warp 5: publishes the scheduler's insertion batches, oldest first, every
-// batch pending at the time in one pass: each task's aux word (upstream still
-// to wait for, seq) and a check that every work-ring cell it fills is free (its
-// sequence word reads its position), one fence.acq_rel.gpu for the pass, then
-// the cells' sequence words. The fence orders what the scheduler warp wrote or
-// saw before handing the batches over (log entries; retirements the poller
+// batch pending at the time in one pass: a check that every work-ring cell it
+// fills is free (its sequence word reads its position), one fence.acq_rel.gpu
+// for the pass, then the cells' sequence words. The fence orders what the
+// other warps wrote or saw before the batches were handed over (the loader's
+// done words, the checkers' aux words, log entries, retirements the poller
 // acquired) before the new units. A pass costs about one fence whatever the
 // number of batches, so batches that queue while one is published go out
 // together in the next.
@@ -618,21 +652,11 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         // read by its worker before that unit's task retired (the fence below
         // orders this read of head_pos before the cells are written)
         const uint32_t head_pos = sole_producer ? lds_volatile(&S.sh->head_pos) : 0u;
-        // 1. every pending batch: aux words, then its cells checked free
+        // 1. every pending batch: its cells checked free
         bool ok = true;
         for (uint32_t b = done_b; b != prod && ok; ++b) {
             const PubBatch &B = S.pub->b[b % kPubSlots];
-            const uint32_t nins = B.nins, p0 = B.p0, total = B.total;
-            if (lane < nins) {
-                const uint32_t q = B.q[lane];
-                const uint32_t gidx = (stream << P.cap_log2) | (q & (C - 1));
-                const unsigned long long up = B.up[lane];
-                *reinterpret_cast<uint4 *>(&P.taskaux[gidx]) = make_uint4((uint32_t)up, (uint32_t)(up >> 32), q, 0u);
-                // the slot's done word names the task with all its CTAs to go
-                // (its previous task retired; waiters may still read the word)
-                st_relaxed_u64(&P.done[stream * kMaxWindow + q % P.window],
-                               ((unsigned long long)(q + 1u) << 32) | B.n[lane]);
-            }
+            const uint32_t p0 = B.p0, total = B.total;
             for (uint32_t u = lane; u < total && ok; u += 32) {
                 const uint32_t x = p0 + u;
                 if (sole_producer && (int32_t)(x - ncells - head_pos) < 0) continue;
@@ -751,6 +775,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             head += run;
             hslot += run;
             if (hslot >= W) hslot -= W;
+            if (lane == 0 && run) sts_volatile(&S.sh->released, head);   // a hint for the checkers
             if (sole_producer && run) {
                 // every unit below the first one of the oldest unreleased task
                 // belongs to a retired task, so its worker has read it
@@ -786,7 +811,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
         // values of this iteration's insertion batch, handed to the publisher below
         bool mine = false;
         uint32_t q = 0, my_n = 0, my_off = 0, js = 0, p0 = 0, total = 0;
-        unsigned long long my_up = 0;
         // 3. insert and dispatch, lane k taking task next + k. Every task is
         //    dispatched when it enters the window: its worker CTAs wait for the
         //    checker's mask and then for the done words of the predecessors it
@@ -797,14 +821,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             mine = lane < nins;
             q = next + lane;
             my_n = mine ? (uint32_t)S.hist[q & HM].r.ncta : 0u;
-            // upstream = candidates still active (older new tasks included);
-            // retired ones were released above
-            unsigned long long act = __ballot_sync(0xffffffffu, st0 == kExec);
-            if (W > 32) act |= (unsigned long long)__ballot_sync(0xffffffffu, st1 == kExec) << 32;
-            const unsigned long long pre = mine ? S.pmask[q & HM] : 0ull;
-            const unsigned long long low = (1ull << lane) - 1ull;
-            const unsigned long long newer = nslot ? (((low << nslot) | (low >> (W - nslot))) & full) : low;
-            const unsigned long long up = pre & (act | newer);
+            // the checker's candidate mask, for the log (the task's workers
+            // read it from its aux word, which the checker wrote)
+            const unsigned long long pre = (mine && logging) ? S.pmask[q & HM] : 0ull;
             // exclusive prefix sum of the CTA counts, one ballot per bit plane
             // (independent of each other, unlike a shuffle scan)
             const uint32_t planes = 32u - (uint32_t)__clz(__reduce_or_sync(0xffffffffu, my_n));
@@ -829,7 +848,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             js = nslot + lane >= W ? nslot + lane - W : nslot + lane;
             my_off = excl;
             if (mine) {
-                my_up = up;
                 S.slotpos[js] = p0 + my_off;
                 if (logging || tracing) {
                     const size_t li = lbase + (q & LM);
@@ -890,7 +908,6 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
             PubBatch &B = S.pub->b[pub_prod % kPubSlots];
             if (mine) {
-                B.up[lane] = my_up;
                 B.q[lane] = q;
                 B.off[lane] = my_off;
                 B.n[lane] = my_n;
@@ -1256,7 +1273,6 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
         const uint32_t gidx = payload >> 8, cta = payload & 255u;
         const uint32_t stream = gidx >> P.cap_log2;
         const uint32_t seq = s_seq;
-        const uint32_t slot = seq % W;
         if (gidx >= nrec) {   // self-check: payload names a ring entry
             if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerPayload);
             continue;
@@ -1273,11 +1289,13 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
-        // wait until every upstream task still active at dispatch completed: the
-        // task in slot b is seq - ((seq - b) mod W) (see slot_done)
+        // wait until every conflicting candidate completed: the candidate in
+        // window slot b is task seq - ((seq - b) mod W), its done word at that
+        // task's ring position (one that retired long ago reads as complete)
         const unsigned long long up = s_up;
         if (up && threadIdx.x < 32) {
-            const unsigned long long *done = P.done + stream * kMaxWindow;
+            const uint32_t CM = (1u << P.cap_log2) - 1u;
+            const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
             const bool w0 = (up >> lane) & 1ull, w1 = lane + 32 < W && ((up >> (lane + 32)) & 1ull);
             const uint32_t i0 = seq - ((seq - lane + 64u * W) % W) + 1u;
             const uint32_t i1 = seq - ((seq - lane - 32u + 64u * W) % W) + 1u;
@@ -1287,8 +1305,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                 bool ok = true;
                 // acquire loads of the done words (released by every CTA of the
                 // upstream tasks); the barrier below passes them to the CTA
-                if (w0) ok = slot_done(ld_acquire_u64(&done[lane]), i0);
-                if (w1) ok = ok && slot_done(ld_acquire_u64(&done[lane + 32]), i1);
+                if (w0) ok = slot_done(ld_acquire_u64(&done[(i0 - 1u) & CM]), i0);
+                if (w1) ok = ok && slot_done(ld_acquire_u64(&done[(i1 - 1u) & CM]), i1);
                 if (__all_sync(0xffffffffu, ok)) break;
                 if ((++spins & 7) == 0) {
                     const bool stop = stopped(P);
@@ -1326,7 +1344,8 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
             const size_t li = ((size_t)stream << P.log_log2) + (seq & ((1u << P.log_log2) - 1u));
             if (tracing) atomicMax(&P.trace[li * kTraceFields + 3], globaltimer_ns());
             if (logging) atomicMax(&P.log_retire[li], atomicAdd(&P.ctl->ticket, 1ull));
-            red_release_add_u64(&P.done[stream * kMaxWindow + slot], ~0ull);   // - 1 in the low half
+            red_release_add_u64(&P.done[((size_t)stream << P.cap_log2) | (seq & ((1u << P.cap_log2) - 1u))],
+                                ~0ull);   // - 1 in the low half
         }
     }
 }

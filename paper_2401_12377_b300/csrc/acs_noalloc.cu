@@ -53,7 +53,7 @@ constexpr size_t kOffCells = kOffRing + up(sizeof(TaskRec) * ACS_NOALLOC_MAX_TAS
 constexpr size_t kOffAux = kOffCells + up(sizeof(unsigned long long) * kNoAllocCells);
 constexpr size_t kOffCtl = kOffAux + up(sizeof(TaskAux) * ACS_NOALLOC_MAX_TASKS);
 constexpr size_t kOffDone = kOffCtl + up(sizeof(DevCtl));
-constexpr size_t kOffLog = kOffDone + up(sizeof(unsigned long long) * kMaxWindow);   // 3 x 1 entry
+constexpr size_t kOffLog = kOffDone + up(sizeof(unsigned long long) * ACS_NOALLOC_MAX_TASKS);   // 3 x 1 entry
 constexpr size_t kOffTrace = kOffLog + up(3 * sizeof(unsigned long long));
 constexpr size_t kOffStats = kOffTrace + up(kTraceFields * sizeof(unsigned long long));
 constexpr size_t kOffStatus = kOffStats + up(sizeof(SchedStats));
@@ -176,7 +176,7 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     HostStatus *status = reinterpret_cast<HostStatus *>(base + kOffStatus);
 
     // what must start from zero: ring cells, counters, done words, status
-    if (launch_init(cells, kNoAllocCells, ctl, done, kMaxWindow, st) != cudaSuccess) return ACS_ERR_DEVICE;
+    if (launch_init(cells, kNoAllocCells, ctl, done, ACS_NOALLOC_MAX_TASKS, st) != cudaSuccess) return ACS_ERR_DEVICE;
     if (cudaMemsetAsync(stats, 0, sizeof(SchedStats), st) != cudaSuccess ||
         cudaMemsetAsync(status, 0, sizeof(HostStatus), st) != cudaSuccess ||
         cudaMemcpyAsync(ring, g_stage, (size_t)n * sizeof(TaskRec), cudaMemcpyHostToDevice, st) != cudaSuccess)

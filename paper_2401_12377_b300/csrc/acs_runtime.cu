@@ -747,8 +747,8 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     chk(cudaHostAlloc(&c->h_ring, nrec * sizeof(TaskRec), cudaHostAllocDefault));
     chk(cudaMalloc(&c->d_ring, nrec * sizeof(TaskRec)));
     chk(cudaMalloc(&c->d_ctl, sizeof(DevCtl)));
-    const uint32_t nslots = c->S * kMaxWindow;
-    chk(cudaMalloc(&c->d_done, nslots * sizeof(unsigned long long)));
+    const uint32_t nslots = c->S * c->C;   // one done word per descriptor ring position
+    chk(cudaMalloc(&c->d_done, (size_t)nslots * sizeof(unsigned long long)));
     // work ring: at most (2W - 1) * ACS_MAX_NCTA units of one stream are in flight
     uint32_t cells = 1;
     while (cells < std::min<uint32_t>(2u * c->W * ACS_MAX_NCTA * std::max<uint32_t>(1u, std::min<uint32_t>(c->S, 8u)), 1u << 20)) cells <<= 1;

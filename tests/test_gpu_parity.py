@@ -427,3 +427,29 @@ def test_rlsim_device_emission_repeats_in_one_context():
             bufs.upload(host)
             assert drv.run() == len(o_tasks)
             assert_same(bufs.download(), o_bufs, "repeated run")
+
+
+# ---- without a log the checkers skip retired candidates (windows past 32) ---------------
+
+@pytest.mark.parametrize("W", [33, 48, 64])
+def test_unlogged_windows_past_32_match_the_oracle(W):
+    """With no log, a checker tests only candidates that had not retired when it
+    ran (the rest would be filtered at insertion anyway). The outputs must stay
+    the oracle's, bit for bit, for partially overlapping elementwise tasks, for
+    the rigid-sphere stream with device emission and for the gated MLP."""
+    s = sg.elementwise_stream(13, n_tasks=400, ranges=True)
+    s.window = W
+    out, _, _ = harness.run_stream(s, log=False)
+    assert_same(out, execute.run_inorder(s.buffers, s.tasks), f"elementwise W={W}")
+    p = sg.RLParams(n_env=256, steps=8)
+    sim = sg.RLSim(3, p)
+    bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+    with harness.Context(W, capacity=1 << 14) as ctx:
+        n = harness.RLEmitDriver(sim, bufs, ctx).run()
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(3, sg.RLParams(n_env=256, steps=8)), emit=True)
+    assert n == len(o_tasks)
+    assert_same(bufs.download(), o_bufs, f"rl emission W={W}")
+    d = sg.dnn_stream(5, batch=4, blocks=12, window=W)
+    out, _, _ = harness.run_stream(d, log=False)
+    ref, _, _ = harness.run_stream(d, mode="inorder")
+    assert_same(out, ref, f"dnn W={W} vs in-order GPU")
