@@ -12,7 +12,7 @@ constexpr int kBlock = ACS_BLOCK_THREADS;
 constexpr int kMaxSegs = ACS_MAX_SEGS;
 constexpr int kMaxWindow = ACS_MAX_WINDOW;
 constexpr int kPrefetch = 16;          // descriptors per prefetch batch (bulk copy)
-constexpr int kBodySmem = 16384;       // shared memory reserved for task bodies
+constexpr int kBodySmem = 24576;       // shared memory reserved for task bodies
 constexpr uint32_t kMinCapacity = 64;
 
 // An inclusive byte range [start, last]; empty segments are never stored.
