@@ -184,8 +184,8 @@ struct alignas(128) Mirror {
 
 // What a worker needs beside its cell's payload, written once per task by the
 // checker warp and indexed like the descriptor ring: the conflicting
-// candidates it must wait for (bit b: the task in window slot b) and the
-// task's seq. Task q + capacity reuses the entry only after task q retired,
+// candidates it must wait for (bit k: the task k + 1 positions earlier) and
+// the task's seq. Task q + capacity reuses the entry only after task q retired,
 // and every CTA of q reads it before q can retire.
 struct alignas(16) TaskAux {
     unsigned long long up;

@@ -451,7 +451,7 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                 }
             }
             __nanosleep(backoff);
-            if (backoff < 256) backoff <<= 1;
+            if (backoff < 64) backoff <<= 1;
         }
     }
 }
@@ -529,7 +529,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
                 }
             }
             __nanosleep(backoff);
-            if (backoff < 256) backoff <<= 1;
+            if (backoff < 64) backoff <<= 1;
         }
         {   // algorithmic bytes: what the task's segments name (lane k: segment k)
             const TaskRec &rr = S.hist[j & HM].r;
@@ -562,28 +562,32 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             c0 = rec_conflict(S.hist[(j - d0) & HM], nt, rj);
         if (d1 <= W - 1 && d1 <= j && (int32_t)(j - d1 - rel) >= 0)
             c1 = rec_conflict(S.hist[(j - d1) & HM], nt, rj);
-        // candidate at distance d sits in slot (j - d) mod W; each lane sets
-        // the bits of its conflicting candidates, two OR reductions merge them
-        const uint32_t js = j % W;
+        // The workers' mask is by distance: bit k for the candidate at distance
+        // k + 1, bit 32 + k for distance k + 33 (two ballots). The log's mask is
+        // by window slot, the candidate at distance d sitting in slot
+        // (j - d) mod W; only a logging launch builds it.
+        const uint32_t dlo = __ballot_sync(0xffffffffu, c0), dhi = __ballot_sync(0xffffffffu, c1);
         uint32_t mlo = 0, mhi = 0;
-        if (c0) {
-            const uint32_t sl = js >= d0 ? js - d0 : js + W - d0;
-            if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
+        if (logging) {
+            const uint32_t js = j % W;
+            if (c0) {
+                const uint32_t sl = js >= d0 ? js - d0 : js + W - d0;
+                if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
+            }
+            if (c1) {
+                const uint32_t sl = js >= d1 ? js - d1 : js + W - d1;
+                if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
+            }
+            mlo = __reduce_or_sync(0xffffffffu, mlo);
+            mhi = __reduce_or_sync(0xffffffffu, mhi);
         }
-        if (c1) {
-            const uint32_t sl = js >= d1 ? js - d1 : js + W - d1;
-            if (sl < 32) mlo |= 1u << sl; else mhi |= 1u << (sl - 32);
-        }
-        mlo = __reduce_or_sync(0xffffffffu, mlo);
-        mhi = __reduce_or_sync(0xffffffffu, mhi);
         if (lane == 0) {
-            const unsigned long long m = (unsigned long long)mlo | ((unsigned long long)mhi << 32);
-            S.pmask[j & HM] = m;
+            if (logging) S.pmask[j & HM] = (unsigned long long)mlo | ((unsigned long long)mhi << 32);
             // what the task's worker CTAs wait for: every conflicting candidate
             // (one that has retired by then reads as complete); published to them
             // by the publisher's fence after the task's insertion
             *reinterpret_cast<uint4 *>(&P.taskaux[((size_t)stream << P.cap_log2) | (j & ((1u << P.cap_log2) - 1u))]) =
-                make_uint4(mlo, mhi, j, 0u);
+                make_uint4(dlo, dhi, j, 0u);
             __threadfence_block();
             sts_volatile(&S.ptag[j & HM], j + 1u);
             if (tracing) check_cycles += clock64() - tc0;
@@ -1058,8 +1062,9 @@ __device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, u
 __device__ __forceinline__ Seg seg_of(uint64_t a, uint64_t n) { return Seg{a, a + n - 1}; }
 
 // The emit task of step t (one CTA): appends solves, integrates, the next
-// broadphase and the next emit task after the current end of its stream, then
-// publishes the new end with release semantics. Every global read it needs
+// broadphase and the next emit task after the current end of its stream, and
+// publishes the new end with release semantics in two steps (the first 32
+// descriptors, then all). Every global read it needs
 // (the cfg block, the island counts, the chunk CTA counts, the stream's end
 // and oldest unreleased task) is issued at once, so the task costs one memory
 // round trip before it writes.
@@ -1159,7 +1164,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     base = E.base;
     const acs_rl_emit_cfg &cfg = E.cfg;
     constexpr uint64_t kPos = 32 * 3 * 4, kProp = 32 * 2 * 4, kRec = ACS_RL_REC_BYTES;
-    for (uint32_t k = tid; k < n_new; k += kBlock) {
+    auto put = [&](uint32_t k) {
         const uint32_t seq = base + k;
         TaskRec *r = ring + (seq & (C - 1));
         Seg sg[5];
@@ -1196,6 +1201,20 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             sg[3] = seg_of(x.token, 4);
             put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3, 0u);
         }
+    };
+    // Warp 0 writes the first 32 descriptors and publishes them at once, so
+    // that the scheduler loads and checks them while the other warps write the
+    // rest; the full end follows below.
+    const uint32_t k1 = min(n_new, 32u);
+    if (warp == 0) {
+        if (lane < k1) put(lane);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();                   // the warp's descriptors before the partial end
+            st_release_u32(&sc->end, base + k1);
+        }
+    } else {
+        for (uint32_t k = k1 + tid - 32u; k < n_new; k += kBlock - 32u) put(k);
     }
     __syncthreads();
     if (tid == 0) {
@@ -1289,16 +1308,17 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
-        // wait until every conflicting candidate completed: the candidate in
-        // window slot b is task seq - ((seq - b) mod W), its done word at that
-        // task's ring position (one that retired long ago reads as complete)
+        // wait until every conflicting candidate completed: bit k of the mask
+        // names task seq - (k + 1), its done word at that task's ring position
+        // (one that retired long ago reads as complete); i0, i1 are the seq + 1
+        // a lane's two candidates stamp on their done words
         const unsigned long long up = s_up;
         if (up && threadIdx.x < 32) {
             const uint32_t CM = (1u << P.cap_log2) - 1u;
             const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
-            const bool w0 = (up >> lane) & 1ull, w1 = lane + 32 < W && ((up >> (lane + 32)) & 1ull);
-            const uint32_t i0 = seq - ((seq - lane + 64u * W) % W) + 1u;
-            const uint32_t i1 = seq - ((seq - lane - 32u + 64u * W) % W) + 1u;
+            const bool w0 = (up >> lane) & 1ull, w1 = (up >> (lane + 32)) & 1ull;
+            const uint32_t i0 = seq - lane;
+            const uint32_t i1 = seq - lane - 32u;
             uint32_t spins = 0, backoff = 16;
             unsigned long long tw = 0;
             while (true) {
