@@ -221,7 +221,8 @@ typedef struct acs_stats {
                                    entries, [6] hand-off to the publisher warp, [7] progress
                                    and idle bookkeeping */
     uint64_t tasks_emitted;     /* tasks appended on the device by emit tasks */
-    uint64_t device_seg_bytes;  /* segment bytes of every checked task (host- or device-submitted) */
+    uint64_t device_seg_bytes;  /* window mode: segment bytes of every task, submitted by the
+                                   host (seg_bytes) or appended on the device by emit tasks */
     uint64_t check_cycles;      /* ACS_FLAG_TRACE: SM cycles the checker warps spent testing */
     uint64_t starved_iters;     /* ACS_FLAG_TRACE: scheduler iterations with a free slot but no
                                    checked task */

@@ -75,11 +75,16 @@ __host__ __device__ inline void fold_reads(TaskRec &r) {
 // A descriptor in a scheduler's shared-memory history, padded to 336 bytes so
 // that 16-byte segment loads of consecutive records by the lanes of a warp hit
 // distinct banks.
+// For a narrow record the loader also writes the low 32 bits of its segments'
+// starts into r.seg[4] and of their lasts into r.seg[5] (four words each,
+// unused entries 0): entries a narrow record never uses, so that a checker
+// reads a candidate in three 16-byte loads (these two and hi .. nsw).
 struct alignas(16) HistRec {
     TaskRec r;
     uint32_t hi;        // the upper 32 address bits of every segment, when `narrow`
     uint32_t narrow;    // 1: at most 4 segments, each inside the 4 GiB window [hi << 32, (hi + 1) << 32)
-    uint32_t pad[2];
+    uint32_t nsw;       // nseg | wmask << 8
+    uint32_t pad;
 };
 static_assert(sizeof(HistRec) == 336, "HistRec layout");
 
@@ -131,7 +136,7 @@ struct SchedStats {
     unsigned long long inserts;
     unsigned long long iterations;
     unsigned long long phase[kPhases];
-    unsigned long long seg_bytes;   // read + write segment bytes of the checked tasks
+    unsigned long long seg_bytes;   // read + write segment bytes of the tasks emitters appended
     unsigned long long emitted;     // descriptors appended by device-side emitters
     unsigned long long check_cycles;    // tracing: cycles checker warps spent testing
     unsigned long long starved_iters;   // tracing: iterations with a free slot but no checked task

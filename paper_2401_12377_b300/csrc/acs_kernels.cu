@@ -64,6 +64,15 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// CTA scope on shared memory: flags between the warps of a scheduler CTA
+__device__ __forceinline__ uint32_t ld_acquire_cta_shared(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta_shared(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // Bulk prefetch of [p, p + bytes) into L2 (a hint: no data moves to the SM);
 // p and bytes multiples of 16.
@@ -195,6 +204,7 @@ struct NewTask {
     Seg a[kRegSegs];
     uint32_t n, w;
     uint32_t hi, narrow;   // as HistRec
+    uint32_t s[kRegSegs], l[kRegSegs];   // narrow: low 32 bits of the starts and lasts
 };
 
 __device__ __forceinline__ NewTask load_new_task(const HistRec &hj) {
@@ -206,13 +216,22 @@ __device__ __forceinline__ NewTask load_new_task(const HistRec &hj) {
     t.narrow = hj.narrow;
 #pragma unroll
     for (int x = 0; x < kRegSegs; ++x) t.a[x] = x < (int)t.n ? rj.seg[x] : Seg{0, 0};   // unused beyond n
+    if (t.narrow) {
+        const uint4 cs = *reinterpret_cast<const uint4 *>(&rj.seg[4]), cl = *reinterpret_cast<const uint4 *>(&rj.seg[5]);
+        t.s[0] = cs.x; t.s[1] = cs.y; t.s[2] = cs.z; t.s[3] = cs.w;
+        t.l[0] = cl.x; t.l[1] = cl.y; t.l[2] = cl.z; t.l[3] = cl.w;
+    } else {
+#pragma unroll
+        for (int x = 0; x < kRegSegs; ++x) { t.s[x] = 0; t.l[x] = 0; }
+    }
     return t;
 }
 
 // Whether every segment of a record lies in one 4 GiB-aligned window (and
 // there are at most kRegSegs of them): then overlap tests against another such
 // record in the same window compare the low 32 bits only, which decide them
-// exactly. Computed once per record by the loader.
+// exactly. Computed once per record by the loader, with the compact 32-bit
+// copies of a narrow record's segments (see HistRec).
 __device__ __forceinline__ void set_narrow(HistRec &h) {
     const uint32_t n = min((uint32_t)h.r.nseg, (uint32_t)kMaxSegs);
     const uint32_t hi = n ? (uint32_t)(h.r.seg[0].start >> 32) : 0u;
@@ -221,6 +240,17 @@ __device__ __forceinline__ void set_narrow(HistRec &h) {
         ok = (uint32_t)(h.r.seg[k].start >> 32) == hi && (uint32_t)(h.r.seg[k].last >> 32) == hi;
     h.hi = hi;
     h.narrow = ok ? 1u : 0u;
+    h.nsw = n | ((uint32_t)h.r.wmask << 8);
+    if (ok) {
+        uint32_t s4[kRegSegs], l4[kRegSegs];
+#pragma unroll
+        for (int k = 0; k < kRegSegs; ++k) {
+            s4[k] = (uint32_t)k < n ? (uint32_t)h.r.seg[k].start : 0u;
+            l4[k] = (uint32_t)k < n ? (uint32_t)h.r.seg[k].last : 0u;
+        }
+        *reinterpret_cast<uint4 *>(&h.r.seg[4]) = make_uint4(s4[0], s4[1], s4[2], s4[3]);
+        *reinterpret_cast<uint4 *>(&h.r.seg[5]) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+    }
 }
 
 // Every segment pair of a candidate (ri) and the new task (t, all segments
@@ -239,33 +269,38 @@ __device__ __noinline__ bool rec_conflict_all(const TaskRec &ri, const TaskRec &
     return false;
 }
 
-// The candidate's first kRegSegs segments are loaded together and every pair
-// with the new task's registers is tested (predicated, no early exit): on the
-// low 32 address bits when both records lie in the same 4 GiB window, else on
-// the full 64 bits.
+// Every segment pair of the candidate and the new task is tested (predicated,
+// no early exit): when both records lie in the same 4 GiB window, on the low
+// 32 address bits from their compact copies (three 16-byte loads of the
+// candidate); else on the full 64 bits of the candidate's first kRegSegs
+// segments, loaded together, and on the rest from shared memory.
 __device__ __forceinline__ bool rec_conflict(const HistRec &hi_, const NewTask &t, const TaskRec &rj) {
     const TaskRec &ri = hi_.r;
+    const uint4 meta = *reinterpret_cast<const uint4 *>(&hi_.hi);   // hi, narrow, nsw, pad
+    if (t.narrow && meta.y && meta.x == t.hi) {
+        const uint4 cs = *reinterpret_cast<const uint4 *>(&ri.seg[4]), cl = *reinterpret_cast<const uint4 *>(&ri.seg[5]);
+        const uint32_t bs[kRegSegs] = {cs.x, cs.y, cs.z, cs.w}, bl[kRegSegs] = {cl.x, cl.y, cl.z, cl.w};
+        const uint32_t ni = meta.z & 0xffu, wi = meta.z >> 8;
+        bool hx[kRegSegs];
+#pragma unroll
+        for (int x = 0; x < kRegSegs; ++x) {
+            const uint32_t as = t.s[x], al = t.l[x];
+            const bool xw = (t.w >> x) & 1u;
+            bool h = false;
+#pragma unroll
+            for (int y = 0; y < kRegSegs; ++y)
+                h |= (uint32_t)y < ni && (xw || ((wi >> y) & 1u)) && as <= bl[y] && bs[y] <= al;
+            hx[x] = (uint32_t)x < t.n && h;
+        }
+        return (hx[0] || hx[1]) || (hx[2] || hx[3]);
+    }
     const uint32_t ni = min((uint32_t)ri.nseg, (uint32_t)kMaxSegs);
     const uint32_t wi = ri.wmask;
     Seg b[kRegSegs];
 #pragma unroll
     for (int y = 0; y < kRegSegs; ++y) b[y] = ri.seg[y];    // unused entries are masked below
     bool hit = false;
-    if (t.narrow && hi_.narrow && hi_.hi == t.hi) {
-        bool hx[kRegSegs];
-#pragma unroll
-        for (int x = 0; x < kRegSegs; ++x) {
-            const uint32_t as = (uint32_t)t.a[x].start, al = (uint32_t)t.a[x].last;
-            const bool xw = (t.w >> x) & 1u;
-            bool h = false;
-#pragma unroll
-            for (int y = 0; y < kRegSegs; ++y)
-                h |= (uint32_t)y < ni && (xw || ((wi >> y) & 1u)) && as <= (uint32_t)b[y].last &&
-                     (uint32_t)b[y].start <= al;
-            hx[x] = (uint32_t)x < t.n && h;
-        }
-        hit = (hx[0] || hx[1]) || (hx[2] || hx[3]);
-    } else {
+    {
 #pragma unroll
         for (int y = 0; y < kRegSegs; ++y) {
             const bool yv = (uint32_t)y < ni, yw = (wi >> y) & 1u;
@@ -503,18 +538,18 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
     constexpr uint32_t kCheckers = kBlock / 32 - 4;   // warps 1 .. 4
     unsigned long long tw = 0;
-    unsigned long long seg_bytes = 0, check_cycles = 0;
+    unsigned long long check_cycles = 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     for (uint32_t j = first + w; open || j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
         uint32_t spins = 0, backoff = 32;
         while (true) {
-            const uint32_t cu = lds_volatile(&S.sh->complete_upto);
+            // an acquire load: the loader released the records below it
+            const uint32_t cu = ld_acquire_cta_shared(&S.sh->complete_upto);
             const uint32_t nx = lds_volatile(&S.sh->next);
             if (cu > j && j < nx + H) break;
             if (lds_volatile(&S.sh->quit)) {
-                if (seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
                 if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
                 return;
             }
@@ -531,17 +566,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             __nanosleep(backoff);
             if (backoff < 64) backoff <<= 1;
         }
-        {   // algorithmic bytes: what the task's segments name (lane k: segment k)
-            const TaskRec &rr = S.hist[j & HM].r;
-            if (lane < min((uint32_t)rr.nseg, (uint32_t)kMaxSegs)) {
-                const Seg g = rr.seg[lane];
-                if (!(g.start == 0 && g.last == ~0ull))
-                    seg_bytes += (g.last - g.start + 1) *
-                                 (1u + (lane < 8 ? ((rr.wmask >> lane) & (rr.flags >> lane) & 1u) : 0u));
-            }
-        }
         tw = 0;
-        __threadfence_block();
         const unsigned long long tc0 = tracing ? clock64() : 0ull;
         const TaskRec &rj = S.hist[j & HM].r;
         if (rj.seq != j || rj.nseg > kMaxSegs) {   // self-check: the record must be task j
@@ -588,13 +613,11 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             // by the publisher's fence after the task's insertion
             *reinterpret_cast<uint4 *>(&P.taskaux[((size_t)stream << P.cap_log2) | (j & ((1u << P.cap_log2) - 1u))]) =
                 make_uint4(dlo, dhi, j, 0u);
-            __threadfence_block();
-            sts_volatile(&S.ptag[j & HM], j + 1u);
+            st_release_cta_shared(&S.ptag[j & HM], j + 1u);   // after the aux word
             if (tracing) check_cycles += clock64() - tc0;
         }
         __syncwarp();
     }
-    if (seg_bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, seg_bytes);
     if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
 }
 
@@ -1035,10 +1058,12 @@ struct EmitSmem {
 static_assert(sizeof(EmitSmem) <= kBodySmem, "emit smem");
 
 // One descriptor written straight into the stream's device ring: header, args
-// and the segments acs_get_addresses derives for the same args.
-__device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, uint16_t ncta, const void *args,
-                                        uint32_t args_bytes, const Seg *segs, uint32_t nseg, uint16_t wmask,
-                                        uint8_t rw) {
+// and the segments acs_get_addresses derives for the same args. Returns the
+// bytes its segments name (a read-modify-write segment twice), as the host
+// counts a submitted task's.
+__device__ __forceinline__ unsigned long long put_rec(TaskRec *r, uint32_t seq, uint16_t op, uint16_t ncta,
+                                                      const void *args, uint32_t args_bytes, const Seg *segs,
+                                                      uint32_t nseg, uint16_t wmask, uint8_t rw) {
     TaskHdr h;
     uint32_t *hw = reinterpret_cast<uint32_t *>(&h);
 #pragma unroll
@@ -1056,7 +1081,12 @@ __device__ __forceinline__ void put_rec(TaskRec *r, uint32_t seq, uint16_t op, u
     const uint4 *src = reinterpret_cast<const uint4 *>(&h);
 #pragma unroll
     for (int i = 0; i < 4; ++i) dst[i] = src[i];
-    for (uint32_t k = 0; k < nseg; ++k) r->seg[k] = segs[k];
+    unsigned long long bytes = 0;
+    for (uint32_t k = 0; k < nseg; ++k) {
+        r->seg[k] = segs[k];
+        bytes += (segs[k].last - segs[k].start + 1) * (1u + ((rw >> k) & 1u));
+    }
+    return bytes;
 }
 
 __device__ __forceinline__ Seg seg_of(uint64_t a, uint64_t n) { return Seg{a, a + n - 1}; }
@@ -1164,6 +1194,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     base = E.base;
     const acs_rl_emit_cfg &cfg = E.cfg;
     constexpr uint64_t kPos = 32 * 3 * 4, kProp = 32 * 2 * 4, kRec = ACS_RL_REC_BYTES;
+    unsigned long long bytes = 0;    // segment bytes of the descriptors this thread writes
     auto put = [&](uint32_t k) {
         const uint32_t seq = base + k;
         TaskRec *r = ring + (seq & (C - 1));
@@ -1176,7 +1207,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             sg[0] = seg_of(x.pos, kPos); sg[1] = seg_of(x.prop, kProp); sg[2] = seg_of(x.cont, kRec);
             sg[3] = seg_of(x.vel, kPos);
             const uint16_t nc = (uint16_t)min(max((uint32_t)E.nisl[k], 1u), 16u);
-            put_rec(r, seq, ACS_OP_RL_SOLVE, nc, &x, sizeof x, sg, 4, 1u << 3, 1u << 3);
+            bytes += put_rec(r, seq, ACS_OP_RL_SOLVE, nc, &x, sizeof x, sg, 4, 1u << 3, 1u << 3);
         } else if (k < n_solve + n_chunks) {
             const uint64_t c = k - n_solve, e0 = c * chunk;
             acs_rl_integrate_args x{cfg.pos + e0 * kPos, cfg.vel + e0 * kPos, cfg.prop + e0 * kProp, chunk,
@@ -1184,14 +1215,14 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             // reads prop, reads and writes pos and vel (the host's folded order)
             sg[0] = seg_of(x.prop, chunk * kProp);
             sg[1] = seg_of(x.pos, chunk * kPos); sg[2] = seg_of(x.vel, chunk * kPos);
-            put_rec(r, seq, ACS_OP_RL_INTEGRATE, E.tab_int[c], &x, sizeof x, sg, 3, 6u, 6u);
+            bytes += put_rec(r, seq, ACS_OP_RL_INTEGRATE, E.tab_int[c], &x, sizeof x, sg, 3, 6u, 6u);
         } else if (k < n_solve + 2 * n_chunks) {
             const uint64_t c = k - n_solve - n_chunks, e0 = c * chunk;
             acs_rl_broadphase_args x{cfg.pos + e0 * kPos, cfg.prop + e0 * kProp, cfg.cont + e0 * kRec,
                                      a.nisl + e0 * 4, chunk, 0};
             sg[0] = seg_of(x.pos, chunk * kPos); sg[1] = seg_of(x.prop, chunk * kProp);
             sg[2] = seg_of(x.cont, chunk * kRec); sg[3] = seg_of(x.nisl, chunk * 4);
-            put_rec(r, seq, ACS_OP_RL_BROADPHASE, E.tab_bp[c], &x, sizeof x, sg, 4, (1u << 2) | (1u << 3), 0u);
+            bytes += put_rec(r, seq, ACS_OP_RL_BROADPHASE, E.tab_bp[c], &x, sizeof x, sg, 4, (1u << 2) | (1u << 3), 0u);
         } else {
             acs_rl_emit_args x = a;
             x.step = a.step + 1;
@@ -1199,7 +1230,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
             sg[1] = seg_of(x.cfg, sizeof(acs_rl_emit_cfg));
             sg[2] = seg_of(x.ncta_table, (uint64_t)(x.steps + 1) * 2 * n_chunks);
             sg[3] = seg_of(x.token, 4);
-            put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3, 0u);
+            bytes += put_rec(r, seq, ACS_OP_RL_EMIT, 1, &x, sizeof x, sg, 4, 1u << 3, 0u);
         }
     };
     // Warp 0 writes the first 32 descriptors and publishes them at once, so
@@ -1216,6 +1247,8 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     } else {
         for (uint32_t k = k1 + tid - 32u; k < n_new; k += kBlock - 32u) put(k);
     }
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0 && bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, bytes);
     __syncthreads();
     if (tid == 0) {
         __threadfence();                       // descriptors before the new end

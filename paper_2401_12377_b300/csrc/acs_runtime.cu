@@ -1259,7 +1259,9 @@ int acs_get_stats(acs_ctx *c, acs_stats *out) {
         if (cudaMemcpy(ss.data(), c->d_sched_stats, c->S * sizeof(SchedStats), cudaMemcpyDeviceToHost) == cudaSuccess) {
             c->stats.sched_cycles = c->stats.sched_busy_cycles = c->stats.sched_inserts = 0;
             c->stats.sched_iterations = 0;
-            c->stats.device_seg_bytes = 0;
+            // the submitted tasks' bytes (counted by acs_submit*) and the
+            // appended ones' (counted by the emitters)
+            c->stats.device_seg_bytes = c->stats.seg_bytes;
             for (int k = 0; k < kPhases; ++k) c->stats.sched_phase_cycles[k] = 0;
             c->stats.check_cycles = c->stats.starved_iters = 0;
             for (auto &x : ss) {

@@ -385,6 +385,13 @@ def test_rlsim_device_emission_small(seed, n_env, steps):
     E = deps.full_dag(segs)
     check_log(masks, start, retire, E, deps.window_dag(E, 32), 32)
     assert_same(out, o_bufs, "device emission vs oracle")
+    # the bytes the tasks' segments name: the host counts the submitted tasks,
+    # the emitters the appended ones; together, the oracle stream's sum plus,
+    # per emit task, its two read-only inputs the oracle's stream leaves out
+    # (the 64-byte cfg block and the CTA-count table, one byte per chunk task)
+    n_emit = sum(t.op == "rl_emit" for t in o_tasks)
+    extra = n_emit * (64 + (steps + 1) * 2 * (n_env // p.chunk))
+    assert st["device_seg_bytes"] == sum(z for r, w in segs for _, z in r + w) + extra
 
 
 def test_rlsim_device_emission_full_size():
