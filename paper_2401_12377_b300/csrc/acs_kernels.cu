@@ -1240,10 +1240,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     if (warp == 0) {
         if (lane < k1) put(lane);
         __syncwarp();
-        if (lane == 0) {
-            __threadfence();                   // the warp's descriptors before the partial end
-            st_release_u32(&sc->end, base + k1);
-        }
+        if (lane == 0) st_release_u32(&sc->end, base + k1);   // the warp's descriptors before it
     } else {
         for (uint32_t k = k1 + tid - 32u; k < n_new; k += kBlock - 32u) put(k);
     }
@@ -1251,8 +1248,7 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
     if (lane == 0 && bytes) atomicAdd(&P.sched_stats[stream].seg_bytes, bytes);
     __syncthreads();
     if (tid == 0) {
-        __threadfence();                       // descriptors before the new end
-        st_release_u32(&sc->end, base + n_new);
+        st_release_u32(&sc->end, base + n_new);   // every descriptor before the new end
         atomicAdd(&P.sched_stats[stream].emitted, (unsigned long long)n_new);
         if (!more) {
             __threadfence();                   // the final end before the stream closes
