@@ -85,7 +85,7 @@ def parse():
 # (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3554304, "sources_sha1": "b1a03db19701bb5219808915e696c42bc3eb6e47"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3570688, "sources_sha1": "66586ba61fa57d15671f88c613cc69918f71bea8"}
 
 
 def kernel_sources_sha1() -> str:
