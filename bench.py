@@ -76,7 +76,17 @@ def parse():
                     help="rlsim: skip the compact runs of the other workloads (tiny, dnn, batched, serving)")
     ap.add_argument("--serving-seconds", type=float, default=2.0,
                     help="seconds of arrivals in the compact serving run of the default benchmark")
+    ap.add_argument("--lookahead", type=int, default=None,
+                    help="window mode: dispatch lookahead for every context (default: the library's, "
+                         "min(window, 64 - window); 0 turns dispatch ahead off)")
     return ap.parse_args()
+
+
+def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: int = 1) -> int:
+    """The dispatch lookahead a window-mode context runs with (as acs_init resolves it)."""
+    if requested is None:
+        return 0 if (span or n_streams > 1) else min(window, 64 - window)
+    return requested
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
@@ -364,7 +374,8 @@ class ClockSampler:
 class RLBench:
     """One mode (window / inorder / graph) on one device state."""
 
-    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False, span=0, traced=False):
+    def __init__(self, mode, seed, window, cta_slots, timing=True, emit=False, span=0, traced=False,
+                 lookahead=None):
         import torch
         import streamgen as sg
         from paper_2401_12377_b300 import harness
@@ -375,7 +386,7 @@ class RLBench:
         self.pristine = {k: v.clone() for k, v in self.bufs.t.items()}
         self.host_pinned = {k: torch.from_numpy(v.view("uint8").copy()).pin_memory() for k, v in host.items()}
         self.ctx = harness.Context(window, mode=mode, timing=timing, capacity=1 << 14, cta_slots=cta_slots,
-                                   span=span, log=traced, trace=traced)
+                                   span=span, log=traced, trace=traced, lookahead=lookahead)
         self.emit = emit
         self.driver = (harness.RLEmitDriver if emit else harness.RLDriver)(self.sim, self.bufs, self.ctx)
         self.mode = mode
@@ -1339,6 +1350,9 @@ def other_configs(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
 
 def main():
     args = parse()
+    if args.lookahead is not None:
+        from paper_2401_12377_b300 import harness
+        harness.DEFAULT_LOOKAHEAD = args.lookahead
     if args.impl == "reference":
         run_reference(args)
         return
@@ -1408,6 +1422,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "window": args.window, "tasks_per_step": tasks_per_step,
+                       "lookahead": effective_lookahead(args.window, 0, args.lookahead),
                        "mode": "window scheduler, device-side emission: one flush and one launch per run",
                        "flushes_per_step": 1, "cta_slots": st.get("cta_slots"),
                        "grid": st.get("grid"), "l2": "flushed between timed steps (512 MiB write)",
@@ -1495,18 +1510,22 @@ def main():
         line["speedup_vs_sw_host_scheduler"] = ms_sw / ms_step
         swa.ctx.close()
 
-    # ---- window-size sensitivity: ring (span = window) and free-slot (span 64) ---------------
+    # ---- window-size sensitivity: the ring dispatching ahead (the default), the plain ring
+    # (lookahead 0) and free-slot (span 64) ------------------------------------------------------
     if args.window_study:
         study = []
-        for span_mode in ("ring", "free-slot"):
+        for span_mode in ("ring, dispatch ahead", "ring", "free-slot"):
             for W in (8, 16, 32, 64):
                 if span_mode == "free-slot" and W == 64:
                     continue
-                arm = RLBench("window", seed, W, args.cta_slots, emit=True, span=64 if span_mode == "free-slot" else 0)
+                span = 64 if span_mode == "free-slot" else 0
+                la = 0 if span_mode == "ring" else None
+                arm = RLBench("window", seed, W, args.cta_slots, emit=True, span=span, lookahead=la)
                 r = time_arm(arm, max(1, min(args.steps, 3)), 1, flush_buf)
                 ms = statistics.mean(r["ms"])
-                study.append({"window": W, "span": 64 if span_mode == "free-slot" else W, "release": span_mode,
-                              "ms_per_run": ms, "tasks_per_s": (r["tasks"] / max(1, min(args.steps, 3))) / (ms / 1e3)})
+                study.append({"window": W, "span": span or W, "lookahead": effective_lookahead(W, span, la),
+                              "release": span_mode, "ms_per_run": ms,
+                              "tasks_per_s": (r["tasks"] / max(1, min(args.steps, 3))) / (ms / 1e3)})
                 arm.ctx.close()
         line["window_study"] = study
 

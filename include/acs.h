@@ -196,8 +196,24 @@ typedef struct acs_config {
                                of order), and candidates are the unretired tasks among
                                j - M + 1 .. j - 1 (the M bound of the upstream load
                                module); logs then give the masks over M - 1 predecessors */
-    uint32_t reserved[2];   /* must be 0 */
+    uint32_t lookahead;     /* window mode, with span = 0: dispatch tasks ahead of the window.
+                               With L > 0 the scheduler inserts task j (checks it against its
+                               window - 1 predecessors, as in the ring, and publishes its
+                               CTAs to the work ring) once every task <= j - window - L has
+                               retired; j's worker CTAs then wait, besides its conflicting
+                               predecessors, until every task <= j - window has retired
+                               before they run it. What runs, the masks (logs give the same
+                               window DAG as L = 0) and legality are those of the ring;
+                               only the dispatch (claiming a task's CTAs, reading its
+                               descriptor) overlaps the window's wait. window + L <= 64.
+                               0 -> off; ACS_LOOKAHEAD_AUTO (acs_config_default) ->
+                               L = min(window, 64 - window) for one stream, 0 with several
+                               streams or a span (CTAs that wait for their stream's window
+                               would hold workers the other streams could use). */
+    uint32_t reserved[1];   /* must be 0 */
 } acs_config;
+
+#define ACS_LOOKAHEAD_AUTO 0xFFFFFFFFu
 
 typedef struct acs_stats {
     uint64_t tasks_submitted;

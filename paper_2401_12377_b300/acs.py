@@ -57,7 +57,10 @@ class acs_config(C.Structure):
                 ("capacity", C.c_uint32), ("log_capacity", C.c_uint32), ("flags", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("poll_ns", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("idle_limit_ms", C.c_uint32),
-                ("sw_threads", C.c_uint32), ("span", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+                ("sw_threads", C.c_uint32), ("span", C.c_uint32), ("lookahead", C.c_uint32),
+                ("reserved", C.c_uint32 * 1)]
+
+LOOKAHEAD_AUTO = 0xFFFFFFFF
 
 
 class acs_stats(C.Structure):

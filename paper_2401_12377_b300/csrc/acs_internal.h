@@ -152,7 +152,8 @@ struct StreamCtl {
     uint32_t end;        // one past the last published descriptor
     uint32_t open;       // emit tasks whose chain has not finished
     uint32_t head_pub;   // oldest unreleased task (emitters wait for ring space)
-    uint32_t pad;
+    uint32_t admit;      // dispatch ahead: every task below it retired, stored by the
+                         // publisher warp after its gpu-scope fence (workers acquire it)
 };
 
 // Host-mapped words of a resident launch (pinned host memory the device reads
@@ -217,8 +218,12 @@ struct KParams {
     uint32_t cap_log2;        // capacity = 1 << cap_log2
     uint32_t log_log2;        // log_capacity = 1 << log_log2
     uint32_t cell_mask;       // work-ring cells - 1 (power of two)
-    uint32_t window;          // ring span M: slots, and the candidate distance M - 1
+    uint32_t window;          // ring span M: slots (tasks inserted and not released)
     uint32_t active_limit;    // tasks inserted and not retired, at most (<= window)
+    uint32_t check_w;         // candidates: the check_w - 1 previous tasks (log masks by slot
+                              // mod check_w); = window except with dispatch ahead
+    uint32_t admit;           // 1: dispatch ahead: a task's workers wait until every task
+                              // check_w or more positions back retired (StreamCtl::admit)
     uint32_t n_streams;       // = scheduler CTAs (CTA s < n_streams schedules stream s)
     uint32_t flags;
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses
@@ -254,6 +259,10 @@ inline uint32_t sched_smem_bytes(uint32_t window) {
     const uint32_t base = H * 336u + H * 8 + H * 4 + 32 + kMaxWindow * 4 * 2;   // hist, pmask, ptag, sh, expect, slotpos
     return (base + 15u) / 16u * 16u + (uint32_t)sizeof(PubQueue);
 }
+
+// Raises the persistent kernel's dynamic shared-memory limit (process-wide,
+// per-function state) to at least `bytes`; never lowers it (acs_runtime.cu).
+cudaError_t raise_kernel_smem_limit(uint32_t bytes);
 
 inline uint32_t dyn_smem_bytes(uint32_t window) {
     uint32_t s = sched_smem_bytes(window);

@@ -530,11 +530,11 @@ __device__ void poller_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
 
 __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw, uint32_t w) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t W = P.window;
+    const uint32_t W = P.check_w;   // candidates: the W - 1 previous tasks
     const uint32_t first = P.first[stream], end = P.end[stream];
     // open or resident: tasks beyond `end` may still come
     const bool open = P.open[stream] != 0 || P.resident != 0;
-    SchedSmem S = carve(smem_raw, W);
+    SchedSmem S = carve(smem_raw, P.window);
     const uint32_t H = S.H, HM = H - 1;   // H is a power of two
     constexpr uint32_t kCheckers = kBlock / 32 - 4;   // warps 1 .. 4
     unsigned long long tw = 0;
@@ -638,6 +638,10 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->end = P.end[stream];
         S.sh->head_pos = 0;
         S.sh->released = first;
+        if (P.admit) {   // dispatch ahead: every task below `first` retired in earlier launches
+            P.sctl[stream].admit = first;
+            __threadfence();
+        }
         if (P.open[stream] || P.resident) {   // published before any emitter of this launch can run
             StreamCtl *sc = &P.sctl[stream];
             sc->end = P.end[stream];
@@ -664,10 +668,11 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const bool sole_producer = P.n_streams == 1;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     uint32_t done_b = 0, backoff = 32;
+    uint32_t admit_pub = P.first[stream];   // dispatch ahead: the admission point last stored
     const uint32_t ncells = P.cell_mask + 1u;
     while (true) {
         const uint32_t prod = lds_volatile(&S.pub->produced);
-        if (prod == done_b) {
+        if (prod == done_b && !(P.admit && lds_volatile(&S.sh->released) != admit_pub)) {
             if (lds_volatile(&S.sh->quit)) return;
             __nanosleep(backoff);
             if (backoff < 64) backoff <<= 1;
@@ -705,6 +710,9 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
         }
         if (!__all_sync(0xffffffffu, ok)) return;
+        // dispatch ahead: the release point read before the fence, stored after it, so
+        // that a worker that acquires it sees the retired tasks' writes
+        const uint32_t rel = P.admit ? ld_acquire_cta_shared(&S.sh->released) : 0u;
         fence_acq_rel_gpu();
         __syncwarp();
         // 2. the cells of every pending batch
@@ -726,6 +734,10 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
         }
         done_b = prod;
+        if (P.admit && rel != admit_pub) {
+            if (lane == 0) st_relaxed_u32(&P.sctl[stream].admit, rel);
+            admit_pub = rel;
+        }
         __syncwarp();
         if (lane == 0) sts_volatile(&S.pub->consumed, done_b);
     }
@@ -802,7 +814,9 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             head += run;
             hslot += run;
             if (hslot >= W) hslot -= W;
-            if (lane == 0 && run) sts_volatile(&S.sh->released, head);   // a hint for the checkers
+            // for the checkers a hint; for the publisher (dispatch ahead) the
+            // release of these retirements, which it passes on to the workers
+            if (lane == 0 && run) st_release_cta_shared(&S.sh->released, head);
             if (sole_producer && run) {
                 // every unit below the first one of the oldest unreleased task
                 // belongs to a retired task, so its worker has read it
@@ -1336,6 +1350,28 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                 for (uint64_t o = 0; o < bytes; o += 32768u)
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
+        }
+        // dispatch ahead: wait until every task W or more positions back retired
+        // (what a ring of W slots ensures before it inserts a task), with an
+        // acquire load of the admission point the publisher stores
+        if (P.admit && threadIdx.x == 0) {
+            const uint32_t need = seq - P.check_w + 1u;
+            const uint32_t *adm = &P.sctl[stream].admit;
+            unsigned long long tw = 0;
+            uint32_t spins = 0, backoff = 16;
+            while ((int32_t)(ld_acquire_u32(adm) - need) < 0) {
+                if ((++spins & 7) == 0) {
+                    if (stopped(P)) break;
+                    const unsigned long long now = globaltimer_ns();
+                    if (tw == 0) tw = now;
+                    else if (now - tw > 4ull * P.timeout_ns) {
+                        raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
+                        break;
+                    }
+                }
+                __nanosleep(backoff);
+                if (backoff < 64) backoff <<= 1;
+            }
         }
         // wait until every conflicting candidate completed: bit k of the mask
         // names task seq - (k + 1), its done word at that task's ring position

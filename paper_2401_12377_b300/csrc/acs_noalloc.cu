@@ -83,10 +83,9 @@ int setup_device(int dev, DeviceSetup &d) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, acs_noalloc_scratch) != cudaSuccess || !p) return ACS_ERR_DEVICE;
     const void *kfn = persistent_kernel_fn();
-    // the largest dynamic shared memory any window needs, set once
+    // the largest dynamic shared memory any window needs (only ever raised)
     const uint32_t smem_max = dyn_smem_bytes(kMaxWindow);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
-        return ACS_ERR_DEVICE;
+    if (raise_kernel_smem_limit(smem_max) != cudaSuccess) return ACS_ERR_DEVICE;
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem_max) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
@@ -201,21 +200,18 @@ extern "C" int acs_run_noalloc(uint32_t window, uint32_t n, const uint32_t *task
     P.cell_mask = kNoAllocCells - 1;
     P.window = window;
     P.active_limit = window;
+    P.check_w = window;   // the ring: candidates over window - 1, no dispatch ahead (admit 0)
     P.n_streams = 1;
     P.flags = 0;
     P.sched_smem = sched_smem_bytes(window);
     P.poll_ns = 128;
     P.first[0] = 0;
     P.end[0] = n;
-    // The kernel's shared-memory limit is per-function state that acs_init also
-    // sets (to its own, possibly smaller, size): raise it again when needed.
+    // The kernel's shared-memory limit is per-function state every context
+    // shares and only raises; make sure it covers this launch.
     const void *kfn = persistent_kernel_fn();
     const uint32_t smem = dyn_smem_bytes(kMaxWindow);
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, kfn) != cudaSuccess) return ACS_ERR_DEVICE;
-    if ((uint32_t)fa.maxDynamicSharedSizeBytes < smem &&
-        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return ACS_ERR_DEVICE;
+    if (raise_kernel_smem_limit(smem) != cudaSuccess) return ACS_ERR_DEVICE;
     void *kargs[] = {&P};
     if (cudaLaunchCooperativeKernel(kfn, dim3(d.grid), dim3(kBlock), kargs, smem, st) != cudaSuccess)
         return ACS_ERR_DEVICE;

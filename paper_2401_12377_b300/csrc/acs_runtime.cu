@@ -31,6 +31,22 @@ cudaError_t launch_init(unsigned long long *cells, uint32_t ncells, DevCtl *ctl,
 
 using namespace acs;
 
+// The persistent kernel's dynamic shared-memory limit is per-function state
+// of the process, shared by every context: it is only ever raised (under a
+// lock), so that creating a context with a smaller window never makes a live
+// context's launches fail.
+cudaError_t acs::raise_kernel_smem_limit(uint32_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    const void *kfn = persistent_kernel_fn();
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kfn);
+    if (e != cudaSuccess) return e;
+    if ((uint32_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+
 namespace {
 
 struct StreamState {
@@ -90,7 +106,8 @@ struct PendingPub {
 struct acs_ctx {
     acs_config cfg{};
     uint32_t W = 0, S = 0, C = 0, cap_log2 = 0, LC = 0, log_log2 = 0;
-    uint32_t Wact = 0;   // active limit (the window); W is the ring span
+    uint32_t Wact = 0;   // the window; W is the ring span (free-slot span, or window + ahead)
+    uint32_t ahead = 0;  // dispatch lookahead (0: off)
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -247,7 +264,11 @@ void fill_params(acs_ctx *c, KParams &P) {
     P.log_log2 = c->log_log2;
     P.cell_mask = c->ncells - 1;
     P.window = c->W;
-    P.active_limit = c->Wact;
+    // ring: W = Wact; free-slot: at most Wact tasks active among W slots, candidates over W;
+    // dispatch ahead: W slots, candidates and admission over Wact
+    P.active_limit = c->ahead ? c->W : c->Wact;
+    P.check_w = c->ahead ? c->Wact : c->W;
+    P.admit = c->ahead ? 1u : 0u;
     P.n_streams = c->S;
     P.flags = c->cfg.flags;
     P.sched_smem = sched_smem_bytes(c->W);
@@ -638,6 +659,7 @@ void acs_config_default(acs_config *cfg) {
     cfg->capacity = 8192;
     cfg->timeout_ns = 5000000000ull;
     cfg->device = -1;
+    cfg->lookahead = ACS_LOOKAHEAD_AUTO;
 }
 
 const char *acs_strerror(int code) {
@@ -704,6 +726,14 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     }
     if (window < 1 || window > (uint32_t)kMaxWindow) return ACS_ERR_INVALID;
     if (cfg.span && (cfg.span < window || cfg.span > (uint32_t)kMaxWindow)) return ACS_ERR_INVALID;
+    // dispatch ahead of the window (window mode only; not with a free-slot span)
+    uint32_t ahead = cfg.lookahead;
+    // (auto: single-stream contexts only; with several streams the lookahead's
+    // claimed-but-waiting CTAs hold workers the other streams could use)
+    if (ahead == ACS_LOOKAHEAD_AUTO)
+        ahead = (cfg.span || cfg.mode != ACS_MODE_WINDOW || cfg.n_streams > 1) ? 0u
+                                                                               : std::min(window, (uint32_t)kMaxWindow - window);
+    if (ahead && (cfg.span || cfg.mode != ACS_MODE_WINDOW || ahead > (uint32_t)kMaxWindow - window)) return ACS_ERR_INVALID;
     if (cfg.n_streams > ACS_MAX_STREAMS) return ACS_ERR_INVALID;
     if (cfg.mode > ACS_MODE_SW) return ACS_ERR_INVALID;
     if (cfg.capacity > (1u << 24)) return ACS_ERR_INVALID;
@@ -711,8 +741,9 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     acs_ctx *c = new (std::nothrow) acs_ctx();
     if (!c) return ACS_ERR_NOMEM;
     c->cfg = cfg;
-    c->W = cfg.span ? cfg.span : window;
+    c->W = cfg.span ? cfg.span : window + ahead;
     c->Wact = window;
+    c->ahead = ahead;
     c->S = cfg.n_streams;
     uint32_t cap = std::max<uint32_t>(cfg.capacity, kMinCapacity);
     cap = std::max<uint32_t>(cap, 2u * c->W + kPrefetch);
@@ -790,7 +821,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
         c->smem = std::max<uint32_t>(c->smem, std::min<uint32_t>(want, (uint32_t)per_block_optin));
     }
     const void *kfn = persistent_kernel_fn();
-    chk(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+    chk(raise_kernel_smem_limit(c->smem));
     int per_sm = 0, sms = 0;
     chk(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, c->smem));
     chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));

@@ -124,6 +124,10 @@ MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph"
          "sw": acs.ACS_MODE_SW}
 
 
+# Dispatch lookahead for Contexts created without one (None: the library's default).
+DEFAULT_LOOKAHEAD: Optional[int] = None
+
+
 class Context:
     """An acs_ctx on the current torch CUDA stream (raises on every error)."""
 
@@ -131,7 +135,7 @@ class Context:
                  capacity: int = 0, log: bool = False, timing: bool = False, trace: bool = False,
                  timeout_s: float = 5.0, poll_ns: int = 0, ctas_per_sm: int = 0,
                  cuda_stream: Optional[int] = None, resident: bool = False, idle_limit_ms: int = 0,
-                 sw_threads: int = 0, span: int = 0):
+                 sw_threads: int = 0, span: int = 0, lookahead: Optional[int] = None):
         cfg = acs.acs_config_default()
         cfg.mode = MODES[mode]
         cfg.n_streams = n_streams
@@ -146,6 +150,10 @@ class Context:
         cfg.idle_limit_ms = idle_limit_ms
         cfg.sw_threads = sw_threads
         cfg.span = span
+        if lookahead is None:
+            lookahead = DEFAULT_LOOKAHEAD
+        if lookahead is not None:          # None: the library's default (dispatch ahead, auto)
+            cfg.lookahead = lookahead
         # All device work of the context goes to one stream shared with torch, so
         # torch copies of the task buffers are ordered with the tasks. The legacy
         # default stream has no handle to share: then a torch stream is made
@@ -239,12 +247,12 @@ class Context:
 
 
 def run_stream(stream, mode: str = "window", window: Optional[int] = None, log: bool = False,
-               cta_slots: int = 0, flush_every: int = 0):
+               cta_slots: int = 0, flush_every: int = 0, lookahead: Optional[int] = None):
     """Run one streamgen Stream on the GPU; returns (buffers after, context
     stats, log or None). ``flush_every`` > 0 splits the stream into flushes."""
     bufs = DeviceBuffers(stream.buffers)
     W = window or stream.window
-    with Context(W, mode=mode, log=log, cta_slots=cta_slots) as ctx:
+    with Context(W, mode=mode, log=log, cta_slots=cta_slots, lookahead=lookahead) as ctx:
         ids, packed = pack_tasks(stream.tasks, bufs)
         step = flush_every or len(ids) or 1
         for a in range(0, len(ids), step):

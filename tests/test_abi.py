@@ -102,6 +102,19 @@ def test_init_argument_checks_need_no_device(lib):
     assert lib.acs_init(C.byref(h), 8, C.byref(cfg)) == acs.ACS_ERR_INVALID
 
 
+def test_lookahead_checks_need_no_device(lib):
+    h = C.c_void_p()
+    cfg = acs.acs_config_default()
+    assert cfg.lookahead == acs.LOOKAHEAD_AUTO          # dispatch ahead by default
+    for window, ahead, span, mode in [(32, 33, 0, 0),   # window + lookahead above 64
+                                      (64, 1, 0, 0),
+                                      (8, 4, 16, 0),    # not with a free-slot span
+                                      (8, 4, 0, 1)]:    # window mode only
+        cfg = acs.acs_config_default()
+        cfg.lookahead, cfg.span, cfg.mode = ahead, span, mode
+        assert lib.acs_init(C.byref(h), window, C.byref(cfg)) == acs.ACS_ERR_INVALID, (window, ahead, span, mode)
+
+
 def test_init_without_a_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():

@@ -141,10 +141,13 @@ def test_whole_memory_segment_orders_everything():
     assert all(np.array_equal(out[k], ref[k]) for k in ref)
 
 
-def test_independent_streams_in_one_launch():
+@pytest.mark.parametrize("lookahead", [None, 0, 8])
+def test_independent_streams_in_one_launch(lookahead):
+    """Five streams in one launch; with several streams the default dispatches
+    without lookahead, and an explicit one applies to every stream."""
     streams = [sg.elementwise_stream(50 + i, n_tasks=20 + 13 * i, ranges=bool(i % 2)) for i in range(5)]
     bufs = [harness.DeviceBuffers(s.buffers) for s in streams]
-    with harness.Context(8, n_streams=5, log=True) as ctx:
+    with harness.Context(8, n_streams=5, log=True, lookahead=lookahead) as ctx:
         for i, s in enumerate(streams):
             ctx.submit(s.tasks, bufs[i], stream=i)
         ctx.flush()
@@ -247,3 +250,24 @@ def test_host_abort_mid_stream_stops_cleanly_and_leaves_the_device_usable():
     out, _, _ = harness.run_stream(s2)
     ref = execute.run_inorder(s2.buffers, s2.tasks)
     assert all(np.array_equal(out[k], ref[k]) for k in ref)
+
+
+def test_a_smaller_context_does_not_break_a_larger_one():
+    """The persistent kernel's shared-memory limit is per-function state of the
+    process: creating a context that needs less (a smaller window) after one
+    that needs more (window 32 dispatching ahead, 64 slots) must leave the
+    first one launchable."""
+    s = sg.elementwise_stream(21, n_tasks=120, ranges=True)
+    bufs = harness.DeviceBuffers(s.buffers)
+    with harness.Context(32, log=False) as big:
+        with harness.Context(4, log=False, lookahead=0) as small:
+            small.submit(s.tasks[:10], bufs)
+            small.flush()
+            small.sync()
+        bufs2 = harness.DeviceBuffers(s.buffers)
+        big.submit(s.tasks, bufs2)
+        big.flush()
+        big.sync()
+        ref = execute.run_inorder(s.buffers, s.tasks)
+        out = bufs2.download()
+        assert all(np.array_equal(out[k], ref[k]) for k in ref)

@@ -436,6 +436,46 @@ def test_rlsim_device_emission_repeats_in_one_context():
             assert_same(bufs.download(), o_bufs, "repeated run")
 
 
+# ---- dispatch ahead of the window (acs_config.lookahead) ------------------------------------
+
+@pytest.mark.parametrize("W,L", [(1, 0), (1, 5), (8, 0), (8, 1), (8, 8), (8, 56), (16, 16), (32, 32), (33, 31)])
+def test_dispatch_ahead_keeps_the_window_dag(W, L):
+    """With lookahead L a task is dispatched up to W + L positions past the
+    oldest unreleased one, and its workers wait for the W-window themselves: the
+    logged masks stay the oracle's D_W, every start is legal against E, and the
+    outputs equal the oracle's in-order execution."""
+    for seed in (3, 8):
+        s = sg.elementwise_stream(seed, n_tasks=300, ranges=True)
+        s.window = W
+        E, D = oracle_dags(s)
+        out, st, (masks, start, retire) = harness.run_stream(s, log=True, lookahead=L)
+        check_log(masks, start, retire, E, D, W)
+        assert_same(out, execute.run_inorder(s.buffers, s.tasks), f"W={W} L={L} seed={seed}")
+
+
+def test_dispatch_ahead_rigid_sphere_and_gated_mlp_outputs():
+    """The default (lookahead on) and lookahead 0 give the oracle's rigid-sphere
+    outputs with device emission, and the same gated-MLP outputs as in-order."""
+    p = sg.RLParams(n_env=64, steps=6)
+    o_tasks, o_bufs, _ = execute.run_rlsim(sg.RLSim(2, sg.RLParams(n_env=64, steps=6)), emit=True)
+    for L in (0, None, 7):
+        sim = sg.RLSim(2, p)
+        bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+        with harness.Context(32, log=True, capacity=1 << 14, lookahead=L) as ctx:
+            n = harness.RLEmitDriver(sim, bufs, ctx).run()
+            masks, start, retire = ctx.log(0, 0, n)
+        assert n == len(o_tasks)
+        segs = addresses.stream_segments(o_tasks, o_bufs)
+        E = deps.full_dag(segs)
+        check_log(masks, start, retire, E, deps.window_dag(E, 32), 32)
+        assert_same(bufs.download(), o_bufs, f"rl emission, lookahead {L}")
+    d = sg.dnn_stream(6, batch=2, blocks=10, window=32)
+    ref, _, _ = harness.run_stream(d, mode="inorder")
+    for L in (0, None):
+        out, _, _ = harness.run_stream(d, lookahead=L)
+        assert_same(out, ref, f"dnn, lookahead {L}")
+
+
 # ---- without a log the checkers skip retired candidates (windows past 32) ---------------
 
 @pytest.mark.parametrize("W", [33, 48, 64])
