@@ -95,7 +95,7 @@ def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: i
 # (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3570688, "sources_sha1": "66586ba61fa57d15671f88c613cc69918f71bea8"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3684608, "sources_sha1": "e20a732501576d70a72c84b0faf3e01e28f256c8"}
 
 
 def kernel_sources_sha1() -> str:
