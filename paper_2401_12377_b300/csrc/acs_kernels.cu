@@ -1351,23 +1351,37 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
-        // dispatch ahead: wait until every task W or more positions back retired
-        // (what a ring of W slots ensures before it inserts a task), with an
-        // acquire load of the admission point the publisher stores
-        if (P.admit && threadIdx.x == 0) {
-            const uint32_t need = seq - P.check_w + 1u;
+        // dispatch ahead: wait until every task W or more positions back
+        // completed (what a ring of W slots ensures before it inserts a task).
+        // The tasks below the admission point the publisher stores (after its
+        // fence; an acquire load here) have; the up to 32 tasks between it and
+        // the window's lower end are checked through their done words (acquire
+        // loads, lane k: task need - 1 - k), so a unit need not wait for the
+        // retirements to travel poller -> scheduler warp -> publisher -> here.
+        if (P.admit && threadIdx.x < 32) {
+            const uint32_t need = seq - P.check_w + 1u;   // every task below it complete
             const uint32_t *adm = &P.sctl[stream].admit;
+            const uint32_t CM = (1u << P.cap_log2) - 1u;
+            const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
             unsigned long long tw = 0;
             uint32_t spins = 0, backoff = 16;
-            while ((int32_t)(ld_acquire_u32(adm) - need) < 0) {
+            while (true) {
+                uint32_t a = 0;
+                if (lane == 0) a = ld_acquire_u32(adm);
+                a = __shfl_sync(0xffffffffu, a, 0);
+                if ((int32_t)(a - need) >= 0) break;
+                if ((int32_t)(need - a) <= 32) {
+                    const uint32_t t = need - 1u - lane;
+                    const bool ok = (int32_t)(t - a) < 0 || slot_done(ld_acquire_u64(&done[t & CM]), t + 1u);
+                    if (__all_sync(0xffffffffu, ok)) break;
+                }
                 if ((++spins & 7) == 0) {
-                    if (stopped(P)) break;
+                    const bool stop = stopped(P);
                     const unsigned long long now = globaltimer_ns();
                     if (tw == 0) tw = now;
-                    else if (now - tw > 4ull * P.timeout_ns) {
-                        raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
-                        break;
-                    }
+                    const bool expired = now - tw > 4ull * P.timeout_ns;
+                    if (expired && lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
+                    if (__any_sync(0xffffffffu, stop || expired)) break;
                 }
                 __nanosleep(backoff);
                 if (backoff < 64) backoff <<= 1;
