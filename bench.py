@@ -95,7 +95,7 @@ def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: i
 # (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3684608, "sources_sha1": "e20a732501576d70a72c84b0faf3e01e28f256c8"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3750912, "sources_sha1": "d360d8a3d88755d22c7c037179957eb8ee5931b0"}
 
 
 def kernel_sources_sha1() -> str:
