@@ -421,10 +421,10 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
                     continue;
                 }
             }
-            // an open stream grows when an emitter publishes a larger end
-            const uint32_t e = ld_relaxed_u32(&P.sctl[stream].end);
+            // an open stream grows when an emitter publishes a larger end (an
+            // acquire load: the emitter's descriptors are visible once it reads it)
+            const uint32_t e = ld_acquire_u32(&P.sctl[stream].end);
             if ((int32_t)(e - end) > 0) {
-                fence_acq_rel_gpu();               // the emitter's descriptors are visible
                 __syncwarp();
                 end = e;
                 if (lane == 0) sts_volatile(&S.sh->end, end);
