@@ -692,7 +692,8 @@ def per_input_bench(args, torch, dist, world, rank, peaks, peak_src, flush_buf, 
     line = {"metric": METRIC, "value": whole_job_rate(world, tps, max_ms / 1e3), "unit": "tasks/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "window": W, "inputs_per_step": len(lat) // args.steps,
+            "config": {"workload": workload, "window": W, "lookahead": effective_lookahead(W, 0, args.lookahead),
+                       "inputs_per_step": len(lat) // args.steps,
                        "tasks_per_step": tps, "cta_slots": st.get("cta_slots"),
                        "mode": "window scheduler, one flush and one persistent launch per input",
                        "l2": "flushed between timed steps (512 MiB write)" + extra_l2,
@@ -988,7 +989,8 @@ def bench_tiny(args, torch, dist, world, rank, peaks, peak_src, flush_buf, n_str
             "config": {"workload": f"tiny elementwise streams: {n_streams} streams (seeds 0..{n_streams - 1}) of 64 "
                                    "FP32 axpy/scale/add tasks over 16 buffers x 4096 floats, 1-4 CTAs per task, "
                                    "window 8, one flush and one launch per stream, back to back",
-                       "window": W, "streams_per_step": n_streams, "tasks_per_step": tps,
+                       "window": W, "lookahead": effective_lookahead(W, 0, args.lookahead),
+                       "streams_per_step": n_streams, "tasks_per_step": tps,
                        "cta_slots": st.get("cta_slots"),
                        "l2": "inputs (250 MiB arena) larger than L2, and flushed between timed steps"},
             "stream_latency_us": {"p50": float(lus[len(lus) // 2]), "p99": float(lus[int(0.99 * (len(lus) - 1))])},
@@ -1126,7 +1128,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                               "note": "the longest of the 64 streams' chains (logged window DAG, tasks "
                                       "weighted by their body times in a traced pass): the makespan with "
                                       "no scheduling overhead"},
-            "config": {"workload": WORKLOAD_BATCHED, "streams": S, "window": W, "tasks_per_step": tasks_per_step,
+            "config": {"workload": WORKLOAD_BATCHED, "streams": S, "window": W,
+                       "lookahead": effective_lookahead(W, 0, args.lookahead, S), "tasks_per_step": tasks_per_step,
                        "cta_slots": st.get("cta_slots"), "grid": st.get("grid"),
                        "stream_lengths": [sp.target for sp in specs],
                        "mode": "window scheduler, one resident persistent launch for all streams; each "
@@ -1277,7 +1280,8 @@ def bench_serving(args, torch, dist, world, rank, peaks, peak_src):
             "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_SERVING, "requests": n_req, "rate_per_s": args.rate,
-                       "step": "one second of arrivals", "slots": args.slots, "window": W, "budget_gb": 20,
+                       "step": "one second of arrivals", "slots": args.slots, "window": W,
+                       "lookahead": effective_lookahead(W, 0, args.lookahead, args.slots), "budget_gb": 20,
                        "catalogue_types": len(specs), "mean_request_tasks": mean_len,
                        "timing": "host clock (perf_counter) from first arrival to last completion",
                        "l2": "not flushed: a continuous open-loop run over > 126 MB of request data",
