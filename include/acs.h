@@ -202,9 +202,9 @@ typedef struct acs_config {
                                CTAs to the work ring) once every task <= j - window - L has
                                retired; j's worker CTAs then wait, besides its conflicting
                                predecessors, until every task <= j - window has completed
-                               before they run it (read from an admission point the
-                               scheduler publishes, and from the done words of the up to 32
-                               tasks just past it). What runs, the masks (logs give the same
+                               before they run it (read from the done words of the L tasks
+                               in between: every task <= j - window - L had retired when j
+                               was inserted). What runs, the masks (logs give the same
                                window DAG as L = 0) and legality are those of the ring;
                                only the dispatch (claiming a task's CTAs, reading its
                                descriptor) overlaps the window's wait. window + L <= 64.

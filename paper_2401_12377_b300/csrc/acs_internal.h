@@ -152,8 +152,6 @@ struct StreamCtl {
     uint32_t end;        // one past the last published descriptor
     uint32_t open;       // emit tasks whose chain has not finished
     uint32_t head_pub;   // oldest unreleased task (emitters wait for ring space)
-    uint32_t admit;      // dispatch ahead: every task below it retired, stored by the
-                         // publisher warp after its gpu-scope fence (workers acquire it)
 };
 
 // Host-mapped words of a resident launch (pinned host memory the device reads
@@ -223,7 +221,7 @@ struct KParams {
     uint32_t check_w;         // candidates: the check_w - 1 previous tasks (log masks by slot
                               // mod check_w); = window except with dispatch ahead
     uint32_t admit;           // 1: dispatch ahead: a task's workers wait until every task
-                              // check_w or more positions back retired (StreamCtl::admit)
+                              // check_w or more positions back completed (their done words)
     uint32_t n_streams;       // = scheduler CTAs (CTA s < n_streams schedules stream s)
     uint32_t flags;
     uint32_t sched_smem;      // bytes of dynamic shared memory a scheduler uses

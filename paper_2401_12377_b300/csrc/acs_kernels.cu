@@ -638,10 +638,6 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
         S.sh->end = P.end[stream];
         S.sh->head_pos = 0;
         S.sh->released = first;
-        if (P.admit) {   // dispatch ahead: every task below `first` retired in earlier launches
-            P.sctl[stream].admit = first;
-            __threadfence();
-        }
         if (P.open[stream] || P.resident) {   // published before any emitter of this launch can run
             StreamCtl *sc = &P.sctl[stream];
             sc->end = P.end[stream];
@@ -668,11 +664,10 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
     const bool sole_producer = P.n_streams == 1;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     uint32_t done_b = 0, backoff = 32;
-    uint32_t admit_pub = P.first[stream];   // dispatch ahead: the admission point last stored
     const uint32_t ncells = P.cell_mask + 1u;
     while (true) {
         const uint32_t prod = lds_volatile(&S.pub->produced);
-        if (prod == done_b && !(P.admit && lds_volatile(&S.sh->released) != admit_pub)) {
+        if (prod == done_b) {
             if (lds_volatile(&S.sh->quit)) return;
             __nanosleep(backoff);
             if (backoff < 64) backoff <<= 1;
@@ -710,9 +705,6 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
         }
         if (!__all_sync(0xffffffffu, ok)) return;
-        // dispatch ahead: the release point read before the fence, stored after it, so
-        // that a worker that acquires it sees the retired tasks' writes
-        const uint32_t rel = P.admit ? ld_acquire_cta_shared(&S.sh->released) : 0u;
         fence_acq_rel_gpu();
         __syncwarp();
         // 2. the cells of every pending batch
@@ -734,10 +726,6 @@ __device__ void publisher_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             }
         }
         done_b = prod;
-        if (P.admit && rel != admit_pub) {
-            if (lane == 0) st_relaxed_u32(&P.sctl[stream].admit, rel);
-            admit_pub = rel;
-        }
         __syncwarp();
         if (lane == 0) sts_volatile(&S.pub->consumed, done_b);
     }
@@ -814,8 +802,7 @@ __device__ void scheduler_warp(const KParams &P, uint32_t stream, uint8_t *smem_
             head += run;
             hslot += run;
             if (hslot >= W) hslot -= W;
-            // for the checkers a hint; for the publisher (dispatch ahead) the
-            // release of these retirements, which it passes on to the workers
+            // for the checkers: candidates below it need no test
             if (lane == 0 && run) st_release_cta_shared(&S.sh->released, head);
             if (sole_producer && run) {
                 // every unit below the first one of the oldest unreleased task
@@ -1274,17 +1261,21 @@ __device__ void body_rl_emit(const KParams &P, uint32_t stream, const TaskHdr &h
 // ---- worker CTAs ----------------------------------------------------------------
 
 __device__ void worker_loop(const KParams &P, uint8_t *smem) {
-    __shared__ uint32_t s_payload;
+    __shared__ unsigned long long s_cell;
     __shared__ uint32_t s_quit;
-    __shared__ unsigned long long s_up;
-    __shared__ uint32_t s_seq;
+    __shared__ uint4 s_aux;
     __shared__ TaskHdr s_hdr;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const uint32_t ncells = P.cell_mask + 1u;
-    const uint32_t W = P.window;
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5;
     const uint32_t nrec = P.n_streams << P.cap_log2;
+    const uint32_t CM = (1u << P.cap_log2) - 1u;
+    // warps 1 and 2 watch the done words of the tasks at distance d = 1 .. 64
+    // back (lane k of warp 1: d = k + 1; of warp 2: d = k + 33), up to the ring's span
+    const uint32_t d = warp * 32u + lane - 31u;
+    const bool watcher = (warp == 1 || warp == 2) && d <= P.window;
     while (true) {
         if (threadIdx.x == 0) {
             // claim the next work-ring position and wait for its unit
@@ -1311,34 +1302,38 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                 __nanosleep(backoff);
                 if (backoff < P.poll_ns) backoff <<= 1;
             }
-            if (!quit) {
-                const uint32_t g = (uint32_t)(v >> 40);      // payload = gidx << 8 | cta
-                // the aux word and the task's header in one round trip
-                uint4 ax = make_uint4(0u, 0u, ~0u, 0u), h0 = ax, h1 = ax, h2 = ax, h3 = ax;
-                if (g < nrec) {
-                    const uint4 *hr = reinterpret_cast<const uint4 *>(P.recs + g);
-                    ax = __ldcg(reinterpret_cast<const uint4 *>(&P.taskaux[g]));
-                    h0 = __ldcg(hr); h1 = __ldcg(hr + 1); h2 = __ldcg(hr + 2); h3 = __ldcg(hr + 3);
-                }
-                uint4 *hd = reinterpret_cast<uint4 *>(&s_hdr);
-                hd[0] = h0; hd[1] = h1; hd[2] = h2; hd[3] = h3;
-                s_up = (unsigned long long)ax.x | ((unsigned long long)ax.y << 32);
-                s_seq = ax.z;
-                st_relaxed_u64(cell, (unsigned long long)(pos + ncells));  // free for the next lap
-            }
-            s_payload = (uint32_t)(v >> 32);
+            if (!quit) st_relaxed_u64(cell, (unsigned long long)(pos + ncells));  // free for the next lap
+            s_cell = v;
             s_quit = quit;
         }
+        // the barrier passes thread 0's acquire of the cell to every thread
         __syncthreads();
         if (s_quit) break;
-        const uint32_t payload = s_payload;
+        const uint32_t payload = (uint32_t)(s_cell >> 32);
         const uint32_t gidx = payload >> 8, cta = payload & 255u;
-        const uint32_t stream = gidx >> P.cap_log2;
-        const uint32_t seq = s_seq;
         if (gidx >= nrec) {   // self-check: payload names a ring entry
             if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerPayload);
+            __syncthreads();
             continue;
         }
+        const uint32_t stream = gidx >> P.cap_log2;
+        const unsigned long long *done = P.done + (gidx & ~CM);   // the stream's done words
+        // one round trip for the task's header and aux word (warp 0) and the
+        // first look at the done words (warps 1, 2: acquire loads, one per
+        // thread, issued before the unit knows which of them it needs; the
+        // words lie inside the stream's ring, so every load is in bounds)
+        unsigned long long dw = 0;
+        if (warp == 0 && lane < 5) {
+            const uint4 *src = lane < 4 ? reinterpret_cast<const uint4 *>(P.recs + gidx) + lane
+                                        : reinterpret_cast<const uint4 *>(&P.taskaux[gidx]);
+            const uint4 w = __ldcg(src);
+            if (lane < 4) reinterpret_cast<uint4 *>(&s_hdr)[lane] = w;
+            else s_aux = w;
+        }
+        if (watcher) dw = ld_acquire_u64(&done[(gidx - d) & CM]);
+        __syncthreads();
+        const uint32_t seq = s_aux.z;
+        const unsigned long long up = (unsigned long long)s_aux.x | ((unsigned long long)s_aux.y << 32);
         // a GEMV unit's weight rows depend on no task: start moving them into L2
         // now, while the unit may still wait for its upstream tasks
         if (threadIdx.x == 0 && s_hdr.op == ACS_OP_GEMV && cta < s_hdr.ncta) {
@@ -1351,75 +1346,44 @@ __device__ void worker_loop(const KParams &P, uint8_t *smem) {
                     prefetch_l2_bulk(reinterpret_cast<const void *>(a + o),
                                      (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u));
         }
-        // dispatch ahead: wait until every task W or more positions back
-        // completed (what a ring of W slots ensures before it inserts a task).
-        // The tasks below the admission point the publisher stores (after its
-        // fence; an acquire load here) have; the up to 32 tasks between it and
-        // the window's lower end are checked through their done words (acquire
-        // loads, lane k: task need - 1 - k), so a unit need not wait for the
-        // retirements to travel poller -> scheduler warp -> publisher -> here.
-        if (P.admit && threadIdx.x < 32) {
-            const uint32_t need = seq - P.check_w + 1u;   // every task below it complete
-            const uint32_t *adm = &P.sctl[stream].admit;
-            const uint32_t CM = (1u << P.cap_log2) - 1u;
-            const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
-            unsigned long long tw = 0;
-            uint32_t spins = 0, backoff = 16;
-            while (true) {
-                uint32_t a = 0;
-                if (lane == 0) a = ld_acquire_u32(adm);
-                a = __shfl_sync(0xffffffffu, a, 0);
-                if ((int32_t)(a - need) >= 0) break;
-                if ((int32_t)(need - a) <= 32) {
-                    const uint32_t t = need - 1u - lane;
-                    const bool ok = (int32_t)(t - a) < 0 || slot_done(ld_acquire_u64(&done[t & CM]), t + 1u);
-                    if (__all_sync(0xffffffffu, ok)) break;
-                }
-                if ((++spins & 7) == 0) {
-                    const bool stop = stopped(P);
-                    const unsigned long long now = globaltimer_ns();
-                    if (tw == 0) tw = now;
-                    const bool expired = now - tw > 4ull * P.timeout_ns;
-                    if (expired && lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
-                    if (__any_sync(0xffffffffu, stop || expired)) break;
-                }
-                __nanosleep(backoff);
-                if (backoff < 64) backoff <<= 1;
-            }
+        // The unit starts once every task it must follow completed:
+        // - the conflicting candidates: bit d - 1 of the checker's mask names
+        //   task seq - d (d <= check_w);
+        // - with dispatch ahead, every task check_w or more positions back
+        //   (what a ring of check_w slots ensures before it inserts a task).
+        //   The scheduler inserted this task only once every task a whole ring
+        //   span (window) or more back had retired, so the tasks at distance
+        //   check_w .. window - 1 remain; those below the launch's first task
+        //   finished in earlier launches.
+        // A done word shows its task complete (or a later task at the same ring
+        // position, which it takes only after the earlier one retired).
+        bool ok = true;
+        if (watcher) {
+            const uint32_t t = seq - d;
+            bool needed = d <= P.check_w && ((up >> (d - 1u)) & 1ull);
+            if (P.admit && d >= P.check_w && d < P.window)
+                needed = needed || (int32_t)(t - P.first[stream]) >= 0;
+            ok = !needed || slot_done(dw, t + 1u);
         }
-        // wait until every conflicting candidate completed: bit k of the mask
-        // names task seq - (k + 1), its done word at that task's ring position
-        // (one that retired long ago reads as complete); i0, i1 are the seq + 1
-        // a lane's two candidates stamp on their done words
-        const unsigned long long up = s_up;
-        if (up && threadIdx.x < 32) {
-            const uint32_t CM = (1u << P.cap_log2) - 1u;
-            const unsigned long long *done = P.done + ((size_t)stream << P.cap_log2);
-            const bool w0 = (up >> lane) & 1ull, w1 = (up >> (lane + 32)) & 1ull;
-            const uint32_t i0 = seq - lane;
-            const uint32_t i1 = seq - lane - 32u;
+        if (!__syncthreads_and(ok)) {
             uint32_t spins = 0, backoff = 16;
             unsigned long long tw = 0;
             while (true) {
-                bool ok = true;
-                // acquire loads of the done words (released by every CTA of the
-                // upstream tasks); the barrier below passes them to the CTA
-                if (w0) ok = slot_done(ld_acquire_u64(&done[(i0 - 1u) & CM]), i0);
-                if (w1) ok = ok && slot_done(ld_acquire_u64(&done[(i1 - 1u) & CM]), i1);
-                if (__all_sync(0xffffffffu, ok)) break;
-                if ((++spins & 7) == 0) {
-                    const bool stop = stopped(P);
-                    const unsigned long long now = globaltimer_ns();
-                    if (tw == 0) tw = now;
-                    bool expired = now - tw > 4ull * P.timeout_ns;
-                    if (expired && lane == 0) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
-                    if (__any_sync(0xffffffffu, stop || expired)) break;
-                }
                 __nanosleep(backoff);
                 if (backoff < 64) backoff <<= 1;
+                if (!ok) {
+                    ok = slot_done(ld_acquire_u64(&done[(gidx - d) & CM]), seq - d + 1u);
+                    if (!ok && (++spins & 7) == 0) {
+                        const unsigned long long now = globaltimer_ns();
+                        if (tw == 0) tw = now;
+                        const bool expired = now - tw > 4ull * P.timeout_ns;
+                        if (expired) raise_error(P, (uint32_t)ACS_ERR_TIMEOUT, kSiteWorker);
+                        if (expired || stopped(P)) ok = true;   // leave; the run has failed
+                    }
+                }
+                if (__syncthreads_and(ok)) break;
             }
         }
-        __syncthreads();
         if (s_hdr.seq != seq || cta >= s_hdr.ncta) {     // self-check: the unit matches its record
             if (threadIdx.x == 0) raise_error(P, (uint32_t)ACS_ERR_INVALID, kSiteWorkerRecord);
             __syncthreads();
