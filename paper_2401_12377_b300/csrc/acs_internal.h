@@ -11,7 +11,7 @@ namespace acs {
 constexpr int kBlock = ACS_BLOCK_THREADS;
 constexpr int kMaxSegs = ACS_MAX_SEGS;
 constexpr int kMaxWindow = ACS_MAX_WINDOW;
-constexpr int kPrefetch = 16;          // descriptors per prefetch batch (bulk copy)
+constexpr int kPrefetch = 16;          // descriptors per loader batch (one round trip)
 constexpr int kBodySmem = 24576;       // shared memory reserved for task bodies
 constexpr uint32_t kMinCapacity = 64;
 

@@ -315,7 +315,8 @@ __device__ __forceinline__ bool rec_conflict(const HistRec &hi_, const NewTask &
 }
 
 // Warp 7: copies descriptors from the stream's device ring into hist with
-// ordinary loads, a batch of kPrefetch at a time, and publishes them through
+// ordinary loads, a batch of kPrefetch at a time (every load of a batch in
+// flight at once: one round trip), and publishes them through
 // complete_upto after a CTA-scope fence. hist[s mod H] may take seq s once the
 // record it replaces (s - H) is neither a candidate of an unchecked task nor
 // uninserted: s < next + H - W + 1.
@@ -433,19 +434,35 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
             wait = true;
             host_wait = P.resident;                // idle until the host publishes work
         } else {
-            const uint32_t bhi = min((load_upto / kPrefetch + 1) * kPrefetch, end);
+            // a batch ends at a multiple of kPrefetch (so never across the
+            // device ring's end) or at the stream's end
+            const uint32_t nb = min((uint32_t)kPrefetch - (load_upto & (kPrefetch - 1u)), end - load_upto);
+            const uint32_t bhi = load_upto + nb;
             const uint32_t nx = lds_volatile(&S.sh->next);
             if (bhi + W > nx + H + 1) {
                 wait = true;
             } else {
                 tw = 0;
                 backoff = 32;
+                // every load of the batch issued before the first store to
+                // shared memory (one round trip, not one per vector)
                 constexpr uint32_t kRec16 = sizeof(TaskRec) / 16;    // 20 vectors per record
+                constexpr uint32_t kPerLane = (kPrefetch * kRec16 + 31) / 32;
                 const uint32_t n16 = (bhi - load_upto) * kRec16;
                 const uint4 *src = reinterpret_cast<const uint4 *>(recs + (load_upto & (C - 1)));
-                for (uint32_t i = lane; i < n16; i += 32) {
-                    const uint32_t rec = i / kRec16, part = i - rec * kRec16;
-                    reinterpret_cast<uint4 *>(&S.hist[(load_upto + rec) & HM])[part] = __ldcg(src + i);
+                uint4 v[kPerLane];
+#pragma unroll
+                for (uint32_t r = 0; r < kPerLane; ++r) {
+                    const uint32_t i = lane + 32u * r;
+                    if (i < n16) v[r] = __ldcg(src + i);
+                }
+#pragma unroll
+                for (uint32_t r = 0; r < kPerLane; ++r) {
+                    const uint32_t i = lane + 32u * r;
+                    if (i < n16) {
+                        const uint32_t rec = i / kRec16, part = i - rec * kRec16;
+                        reinterpret_cast<uint4 *>(&S.hist[(load_upto + rec) & HM])[part] = v[r];
+                    }
                 }
                 __syncwarp();
                 if (lane < bhi - load_upto) {
