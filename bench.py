@@ -78,14 +78,14 @@ def parse():
                     help="seconds of arrivals in the compact serving run of the default benchmark")
     ap.add_argument("--lookahead", type=int, default=None,
                     help="window mode: dispatch lookahead for every context (default: the library's, "
-                         "min(window, 64 - window); 0 turns dispatch ahead off)")
+                         "min(2 window, 64 - window); 0 turns dispatch ahead off)")
     return ap.parse_args()
 
 
 def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: int = 1) -> int:
     """The dispatch lookahead a window-mode context runs with (as acs_init resolves it)."""
     if requested is None:
-        return 0 if (span or n_streams > 1) else min(window, 64 - window)
+        return 0 if (span or n_streams > 1) else min(2 * window, 64 - window)
     return requested
 
 

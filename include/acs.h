@@ -209,7 +209,7 @@ typedef struct acs_config {
                                only the dispatch (claiming a task's CTAs, reading its
                                descriptor) overlaps the window's wait. window + L <= 64.
                                0 -> off; ACS_LOOKAHEAD_AUTO (acs_config_default) ->
-                               L = min(window, 64 - window) for one stream, 0 with several
+                               L = min(2 window, 64 - window) for one stream, 0 with several
                                streams or a span (CTAs that wait for their stream's window
                                would hold workers the other streams could use). */
     uint32_t reserved[1];   /* must be 0 */

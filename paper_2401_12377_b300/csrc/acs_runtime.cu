@@ -732,7 +732,7 @@ int acs_init(acs_ctx **out, uint32_t window, const acs_config *cfg_in) {
     // claimed-but-waiting CTAs hold workers the other streams could use)
     if (ahead == ACS_LOOKAHEAD_AUTO)
         ahead = (cfg.span || cfg.mode != ACS_MODE_WINDOW || cfg.n_streams > 1) ? 0u
-                                                                               : std::min(window, (uint32_t)kMaxWindow - window);
+                                                                               : std::min(2u * window, (uint32_t)kMaxWindow - window);
     if (ahead && (cfg.span || cfg.mode != ACS_MODE_WINDOW || ahead > (uint32_t)kMaxWindow - window)) return ACS_ERR_INVALID;
     if (cfg.n_streams > ACS_MAX_STREAMS) return ACS_ERR_INVALID;
     if (cfg.mode > ACS_MODE_SW) return ACS_ERR_INVALID;
