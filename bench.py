@@ -432,11 +432,21 @@ def l2_flush(buf):
         buf.zero_()
 
 
+# Warm-up runs go on for at least this long as well as for the requested number
+# of steps: the host CPU needs a few hundred milliseconds of load to come back to
+# full clock after an idle spell (measured on the B300 hosts: a run's host work,
+# submit + flush, takes 25 us at full clock and 140 us right after a 2 s sleep;
+# 50 ms of load recovers half of that, 500 ms all of it).
+HOST_WARM_S = 0.5
+
+
 def time_arm(arm, steps, warmup, flush_buf, latencies=None):
     torch = arm.torch
-    for _ in range(warmup):
+    k, t_warm = 0, time.perf_counter() + HOST_WARM_S
+    while k < warmup or time.perf_counter() < t_warm:
         arm.reset_device()
         arm.run_once()
+        k += 1
     torch.cuda.current_stream().synchronize()
     st0 = arm.ctx.stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -557,14 +567,23 @@ def time_e2e(arm, steps):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out_pos = torch.empty_like(arm.bufs.t["pos"], device="cpu").pin_memory()
     out_vel = torch.empty_like(arm.bufs.t["vel"], device="cpu").pin_memory()
+
+    def step():
+        arm.upload_host()
+        n = arm.run_once()
+        out_pos.copy_(arm.bufs.t["pos"], non_blocking=True)
+        out_vel.copy_(arm.bufs.t["vel"], non_blocking=True)
+        return n
+
+    k, t_warm = 0, time.perf_counter() + HOST_WARM_S      # untimed warm-up, as for every arm
+    while k < 1 or time.perf_counter() < t_warm:
+        step()
+        k += 1
     tasks = 0
     torch.cuda.synchronize()
     ev0.record()
     for _ in range(steps):
-        arm.upload_host()
-        tasks += arm.run_once()
-        out_pos.copy_(arm.bufs.t["pos"], non_blocking=True)
-        out_vel.copy_(arm.bufs.t["vel"], non_blocking=True)
+        tasks += step()
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / steps
@@ -1430,6 +1449,7 @@ def main():
                        "mode": "window scheduler, device-side emission: one flush and one launch per run",
                        "flushes_per_step": 1, "cta_slots": st.get("cta_slots"),
                        "grid": st.get("grid"), "l2": "flushed between timed steps (512 MiB write)",
+                       "warm_up": f"at least {args.warmup} steps and {HOST_WARM_S} s of steps (every arm)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
             "run_latency_us": {"p50": lat_us[len(lat_us) // 2] if lat_us else None,
                                "p99": lat_us[min(len(lat_us) - 1, int(0.99 * len(lat_us)))] if lat_us else None},
