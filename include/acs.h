@@ -43,6 +43,7 @@ extern "C" {
 #define ACS_ERR_STOPPED    (-5)  /* the context was stopped */
 #define ACS_ERR_ORDER      (-6)  /* task_id not strictly increasing within a stream */
 #define ACS_ERR_NOMEM      (-7)  /* host or device allocation failed */
+#define ACS_ERR_RANGE      (-8)  /* the stream's position reached 2^31: acs_stream_rebase first */
 
 /* ---- limits ------------------------------------------------------------- */
 #define ACS_MAX_WINDOW     64    /* W: slots of the scheduling window per stream */
@@ -350,6 +351,20 @@ int acs_get_trace(acs_ctx *ctx, uint32_t stream, uint64_t first, uint32_t n, uin
  * plus device appended, the latter known after acs_sync); the next task's seq.
  * Errors: ACS_ERR_INVALID. */
 int acs_stream_tail(acs_ctx *ctx, uint32_t stream, uint32_t *tail);
+
+/* Restarts an idle stream's positions: its next task gets seq `pos` (normally
+ * 0). Positions are 32-bit and a stream takes host-submitted tasks only below
+ * ACS_MAX_POSITION (2^31; ACS_ERR_RANGE there), which keeps every comparison
+ * of positions on the device, and the seq + 1 words that mark a task done or
+ * checked, clear of the 2^32 wrap; a long-lived stream calls this at an idle
+ * point. Idle: everything submitted was flushed and synced (acs_sync), no
+ * emitter chain is alive, no resident launch runs (acs_stop first). After it
+ * the tasks before `pos` count as complete and are no candidates; the logs and
+ * traces of the earlier tasks are no longer readable and task ids may start
+ * over. pos < ACS_MAX_POSITION.
+ * Errors: ACS_ERR_INVALID (bad stream or pos, not idle, resident launch). */
+#define ACS_MAX_POSITION 0x80000000u
+int acs_stream_rebase(acs_ctx *ctx, uint32_t stream, uint32_t pos);
 
 /*
  * Resident (serving) launches. acs_start launches the persistent scheduler

@@ -23,6 +23,8 @@ ACS_ERR_DEVICE = -4
 ACS_ERR_STOPPED = -5
 ACS_ERR_ORDER = -6
 ACS_ERR_NOMEM = -7
+ACS_ERR_RANGE = -8
+ACS_MAX_POSITION = 1 << 31
 
 ACS_MAX_WINDOW = 64
 ACS_MAX_SEGS = 16
@@ -82,7 +84,7 @@ assert ARGS_DTYPE.itemsize == C.sizeof(acs_args) == 56
 EXPORTS = ["acs_config_default", "acs_init", "acs_get_addresses", "acs_submit", "acs_submit_stream",
            "acs_submit_ops", "acs_flush", "acs_sync", "acs_get_log", "acs_get_trace", "acs_stream_tail",
            "acs_get_stats", "acs_graph_replay", "acs_start", "acs_progress", "acs_stop",
-           "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc", "acs_abort"]
+           "acs_error", "acs_strerror", "acs_destroy", "acs_run_noalloc", "acs_abort", "acs_stream_rebase"]
 
 _lib = None
 
@@ -111,6 +113,7 @@ def load(path: str = LIB_PATH):
                                 C.c_void_p]
     lib.acs_get_trace.argtypes = [C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p]
     lib.acs_stream_tail.argtypes = [C.c_void_p, C.c_uint32, P(C.c_uint32)]
+    lib.acs_stream_rebase.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32]
     lib.acs_get_stats.argtypes = [C.c_void_p, P(acs_stats)]
     lib.acs_graph_replay.argtypes = [C.c_void_p]
     lib.acs_start.argtypes = [C.c_void_p]
@@ -219,6 +222,10 @@ def acs_stream_tail(ctx, stream: int) -> int:
     v = C.c_uint32()
     check(load().acs_stream_tail(ctx, stream, C.byref(v)), "acs_stream_tail")
     return v.value
+
+
+def acs_stream_rebase(ctx, stream: int, pos: int = 0) -> int:
+    return load().acs_stream_rebase(ctx, stream, pos)
 
 
 def acs_start(ctx) -> None:

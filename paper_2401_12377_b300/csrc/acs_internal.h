@@ -233,7 +233,11 @@ struct KParams {
     uint32_t first[ACS_MAX_STREAMS];  // first seq of this launch, per stream
     uint32_t end[ACS_MAX_STREAMS];    // one past the last seq submitted by the host
     uint8_t open[ACS_MAX_STREAMS];    // emit tasks among the stream's new tasks
+    uint8_t nprev[ACS_MAX_STREAMS];   // tasks the stream had before `first` since it was last
+                                      // restarted (acs_stream_rebase), at most 64: the
+                                      // candidates and ring slots below `first` that exist
 };
+static_assert(sizeof(KParams) <= 4096, "KParams fits the classic kernel-parameter limit");
 
 // descriptors kept in a scheduler's shared-memory history ring: the W - 1
 // predecessors of every task being checked plus look-ahead

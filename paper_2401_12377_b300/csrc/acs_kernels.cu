@@ -361,7 +361,7 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
     const TaskRec *recs = P.recs + (size_t)stream * C;
     SchedSmem S = carve(smem_raw, W);
     const uint32_t H = S.H, HM = H - 1;
-    uint32_t load_upto = first > W - 1 ? first - (W - 1) : 0u;
+    uint32_t load_upto = first - min(W - 1u, (uint32_t)P.nprev[stream]);   // the predecessors that exist
     unsigned long long tw = 0;
     uint32_t spins = 0, backoff = 32;
     uint32_t host_seen = end;                      // resident: host end last read
@@ -592,6 +592,7 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         }
         bool c0 = false, c1 = false;
         const uint32_t d0 = lane + 1, d1 = lane + 33;      // distances to the candidates
+        const uint32_t have = j - first + P.nprev[stream];   // tasks of the stream before j (capped)
         const NewTask nt = load_new_task(S.hist[j & HM]);
         // Without a log, a candidate that already retired is not tested: its
         // done word reads as complete to the task's workers anyway, and the
@@ -600,9 +601,9 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
         // only means more tests.) With a log, every candidate is tested: the
         // log holds the window DAG.
         const uint32_t rel = logging ? 0u : lds_volatile(&S.sh->released);
-        if (d0 <= W - 1 && d0 <= j && (int32_t)(j - d0 - rel) >= 0)
+        if (d0 <= W - 1 && d0 <= have && (int32_t)(j - d0 - rel) >= 0)
             c0 = rec_conflict(S.hist[(j - d0) & HM], nt, rj);
-        if (d1 <= W - 1 && d1 <= j && (int32_t)(j - d1 - rel) >= 0)
+        if (d1 <= W - 1 && d1 <= have && (int32_t)(j - d1 - rel) >= 0)
             c1 = rec_conflict(S.hist[(j - d1) & HM], nt, rj);
         // The workers' mask is by distance: bit k for the candidate at distance
         // k + 1, bit 32 + k for distance k + 33 (two ballots). The log's mask is
@@ -649,7 +650,7 @@ __device__ void sched_init(const KParams &P, uint32_t stream, uint8_t *smem_raw)
     if (threadIdx.x == 0) {
         S.pub->produced = 0;
         S.pub->consumed = 0;
-        S.sh->complete_upto = first > W - 1 ? first - (W - 1) : 0u;
+        S.sh->complete_upto = first - min(W - 1u, (uint32_t)P.nprev[stream]);
         S.sh->next = first;
         S.sh->quit = 0;
         S.sh->end = P.end[stream];

@@ -57,7 +57,15 @@ struct StreamState {
     uint32_t last_id = 0;
     uint32_t emit_pending = 0;  // emit tasks submitted since the last flush
     bool emitting = false;      // flushed emit tasks not yet synced: the device owns the end
+    uint32_t base = 0;          // position the stream was last restarted at (acs_stream_rebase)
 };
+
+// tasks a stream had before position `first` since its last restart, capped
+// at 64 (the most predecessors a window tests)
+uint8_t tasks_before(const StreamState &ss, uint32_t first) {
+    const uint32_t n = first - ss.base;
+    return (uint8_t)(n < 64u ? n : 64u);
+}
 
 int64_t wrap_diff(uint32_t a, uint32_t b) { return (int64_t)(int32_t)(a - b); }
 
@@ -307,6 +315,7 @@ int flush_window(acs_ctx *c) {
     fill_params(c, P);
     for (uint32_t s = 0; s < c->S; ++s) {
         P.first[s] = c->st[s].flushed;
+        P.nprev[s] = tasks_before(c->st[s], P.first[s]);
         P.end[s] = c->st[s].submitted;
         P.open[s] = (uint8_t)std::min<uint32_t>(c->st[s].emit_pending, 255u);
     }
@@ -672,6 +681,7 @@ const char *acs_strerror(int code) {
     case ACS_ERR_STOPPED: return "context stopped";
     case ACS_ERR_ORDER: return "task_id not strictly increasing within its stream";
     case ACS_ERR_NOMEM: return "out of memory";
+    case ACS_ERR_RANGE: return "stream position reached 2^31 (acs_stream_rebase at an idle point)";
     default: return "unknown status";
     }
 }
@@ -935,6 +945,7 @@ int acs_submit_stream(acs_ctx *c, uint32_t stream, uint32_t task_id, const acs_a
     if (c->resident && (ss.emitting || full)) refresh_stream(c, stream);
     if (ss.emitting) return ACS_ERR_INVALID;   // sync first: the device appends to this stream
     if (args->op == ACS_OP_RL_EMIT && c->cfg.mode != ACS_MODE_WINDOW) return ACS_ERR_INVALID;
+    if (ss.submitted >= ACS_MAX_POSITION) return ACS_ERR_RANGE;   // acs_stream_rebase at an idle point
     if (ss.has_id && task_id <= ss.last_id) return ACS_ERR_ORDER;
     if ((uint64_t)ss.submitted + c->W - 1 - ss.synced + 1 > c->C - kPrefetch) return ACS_ERR_FULL;
     TaskRec &r = c->h_ring[(size_t)stream * c->C + (ss.submitted & (c->C - 1))];
@@ -1161,6 +1172,7 @@ int acs_start(acs_ctx *c) {
     P.resident = 1;
     for (uint32_t s = 0; s < c->S; ++s) {
         P.first[s] = c->st[s].flushed;
+        P.nprev[s] = tasks_before(c->st[s], P.first[s]);
         P.end[s] = c->st[s].flushed;
         P.open[s] = 0;
     }
@@ -1280,6 +1292,24 @@ int acs_abort(acs_ctx *c) {
 int acs_stream_tail(acs_ctx *c, uint32_t stream, uint32_t *tail) {
     if (!c || !tail || stream >= c->S) return ACS_ERR_INVALID;
     *tail = c->st[stream].submitted;
+    return ACS_OK;
+}
+
+// Nothing on the device that outlives a launch is keyed to the old positions
+// in a way a later launch consults: a launch writes the done words of its own
+// tasks before any of them is published, counts the tasks before its first one
+// as complete (workers' admission) and loads and tests as candidates only the
+// tasks the stream had since its restart (KParams::nprev).
+int acs_stream_rebase(acs_ctx *c, uint32_t stream, uint32_t pos) {
+    if (!c || stream >= c->S || pos >= ACS_MAX_POSITION) return ACS_ERR_INVALID;
+    if (c->err) return c->err;
+    if (c->resident) return ACS_ERR_INVALID;   // acs_stop first
+    StreamState &ss = c->st[stream];
+    if (ss.submitted != ss.flushed || ss.flushed != ss.synced || ss.emitting || ss.emit_pending)
+        return ACS_ERR_INVALID;                // acs_flush + acs_sync first
+    ss.submitted = ss.flushed = ss.synced = ss.base = pos;
+    ss.has_id = false;
+    ss.last_id = 0;
     return ACS_OK;
 }
 

@@ -126,6 +126,9 @@ MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph"
 
 # Dispatch lookahead for Contexts created without one (None: the library's default).
 DEFAULT_LOOKAHEAD: Optional[int] = None
+# a driver restarts an idle stream's positions once they pass this (the library
+# takes host-submitted tasks only below 2^31 per stream)
+REBASE_AT = 1 << 30
 
 
 class Context:
@@ -226,6 +229,10 @@ class Context:
 
     def tail(self, stream: int = 0) -> int:
         return acs.acs_stream_tail(self.h, stream)
+
+    def rebase(self, stream: int = 0, pos: int = 0) -> None:
+        """Restart an idle stream's positions at `pos` (acs_stream_rebase)."""
+        acs.check(acs.acs_stream_rebase(self.h, stream, pos), "acs_stream_rebase")
 
     def replay(self) -> None:
         acs.check(acs.acs_graph_replay(self.h), "acs_graph_replay")
@@ -371,6 +378,8 @@ class RLEmitDriver:
     def submit(self) -> int:
         """Submit the run's first tasks to the context (no flush); returns the
         stream position the run starts at."""
+        if self.ctx.tail(self.stream) >= REBASE_AT:   # idle here: keep positions clear of 2^31
+            self.ctx.rebase(self.stream)
         start = self.ctx.tail(self.stream)
         # emitted tasks take task_id = their position, so ids continue from there
         if self._packed is None:

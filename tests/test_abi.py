@@ -194,3 +194,13 @@ def test_noalloc_valid_tasks_without_a_gpu_fail_cleanly(lib):
         pytest.skip("a GPU is present")
     packed = _noalloc_rows([("axpy", 1, _AXPY)] * 2)
     assert acs.acs_run_noalloc(8, np.array([1, 2], np.uint32), packed) == acs.ACS_ERR_DEVICE
+
+
+def test_stream_rebase_checks_need_no_device(lib):
+    """acs_stream_rebase refuses a missing context; the position-limit error has
+    its own code and message, and the binding's limit is the header's."""
+    assert lib.acs_stream_rebase(None, 0, 0) == acs.ACS_ERR_INVALID
+    hdr = open(os.path.join(ROOT, "include", "acs.h")).read()
+    assert re.search(r"#define ACS_ERR_RANGE\s+\(-8\)", hdr) and acs.ACS_ERR_RANGE == -8
+    assert re.search(r"#define ACS_MAX_POSITION 0x80000000u", hdr) and acs.ACS_MAX_POSITION == 1 << 31
+    assert b"2^31" in lib.acs_strerror(acs.ACS_ERR_RANGE)

@@ -500,3 +500,43 @@ def test_unlogged_windows_past_32_match_the_oracle(W):
     out, _, _ = harness.run_stream(d, log=False)
     ref, _, _ = harness.run_stream(d, mode="inorder")
     assert_same(out, ref, f"dnn W={W} vs in-order GPU")
+
+
+# ---- restarting a stream's positions (acs_stream_rebase) -------------------------------------
+
+@pytest.mark.parametrize("W,L", [(32, None), (8, None), (33, 0), (64, 0)])
+def test_a_restarted_stream_keeps_the_window_dag_and_outputs(W, L):
+    """One context runs the same stream from several positions: 0, just below the
+    2^31 limit, 0 again and a position that is no multiple of the window. Each run
+    finds ring slots, done words and log entries of the previous numbering; the
+    logged masks (by slot, seq mod W) decode to the oracle's D_W, every start is
+    legal against E and the outputs equal the oracle's. Past the limit a
+    submission is refused, and a stream that is not idle cannot be restarted."""
+    s = sg.elementwise_stream(21, n_tasks=300, ranges=True)
+    s.window = W
+    E, D = oracle_dags(s)
+    ref = execute.run_inorder(s.buffers, s.tasks)
+    limit = acs.ACS_MAX_POSITION
+    with harness.Context(W, log=True, capacity=1 << 12, lookahead=L) as ctx:
+        for pos in (0, limit - 1000, 0, 12345):
+            ctx.rebase(0, pos)
+            assert ctx.tail(0) == pos
+            bufs = harness.DeviceBuffers(s.buffers)
+            ids, packed = harness.pack_tasks(s.tasks, bufs)
+            ctx.submit_packed(ids, packed)
+            ctx.flush()
+            ctx.sync()
+            masks, start, retire = ctx.log(0, pos, len(ids))
+            rot = [sum(1 << ((b - pos) % W) for b in range(64) if (int(m) >> b) & 1) for m in masks]
+            check_log(rot, start, retire, E, D, W)
+            assert_same(bufs.download(), ref, f"W={W} L={L} from position {pos}")
+        # at the limit: the last two positions below it are taken, the next is refused
+        ctx.rebase(0, limit - 2)
+        a = harness.pack_tasks(s.tasks[:3], harness.DeviceBuffers(s.buffers))
+        ctx.submit_packed(a[0][:2], a[1][:2])
+        assert acs.acs_submit_ops(ctx.h, 0, np.array([2], np.uint32), a[1][2:3]) == acs.ACS_ERR_RANGE
+        assert acs.acs_stream_rebase(ctx.h, 0, 0) == acs.ACS_ERR_INVALID      # submitted, not synced
+        ctx.flush()
+        ctx.sync()
+        ctx.rebase(0, 0)
+        assert ctx.tail(0) == 0
