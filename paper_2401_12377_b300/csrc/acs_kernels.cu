@@ -281,18 +281,20 @@ __device__ __forceinline__ bool rec_conflict(const HistRec &hi_, const NewTask &
         const uint4 cs = *reinterpret_cast<const uint4 *>(&ri.seg[4]), cl = *reinterpret_cast<const uint4 *>(&ri.seg[5]);
         const uint32_t bs[kRegSegs] = {cs.x, cs.y, cs.z, cs.w}, bl[kRegSegs] = {cl.x, cl.y, cl.z, cl.w};
         const uint32_t ni = meta.z & 0xffu, wi = meta.z >> 8;
-        bool hx[kRegSegs];
+        // which segment pairs count (x and y valid, one of them written) as a
+        // 16-bit mask (bit 4x + y), which overlap as another: one AND decides
+        // (fewer instructions than testing the conditions pair by pair)
+        const uint32_t yv = (1u << ni) - 1u, yw = wi & yv;
+        uint32_t elig = 0, ov = 0;
 #pragma unroll
         for (int x = 0; x < kRegSegs; ++x) {
-            const uint32_t as = t.s[x], al = t.l[x];
-            const bool xw = (t.w >> x) & 1u;
-            bool h = false;
+            const uint32_t ym = (uint32_t)x < t.n ? (((t.w >> x) & 1u) ? yv : yw) : 0u;
+            elig |= ym << (4 * x);
 #pragma unroll
             for (int y = 0; y < kRegSegs; ++y)
-                h |= (uint32_t)y < ni && (xw || ((wi >> y) & 1u)) && as <= bl[y] && bs[y] <= al;
-            hx[x] = (uint32_t)x < t.n && h;
+                ov |= (t.s[x] <= bl[y] && bs[y] <= t.l[x]) ? (1u << (4 * x + y)) : 0u;
         }
-        return (hx[0] || hx[1]) || (hx[2] || hx[3]);
+        return (elig & ov) != 0u;
     }
     const uint32_t ni = min((uint32_t)ri.nseg, (uint32_t)kMaxSegs);
     const uint32_t wi = ri.wmask;
