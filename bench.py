@@ -1545,10 +1545,14 @@ def main():
                 span = 64 if span_mode == "free-slot" else 0
                 la = 0 if span_mode == "ring" else None
                 arm = RLBench("window", seed, W, args.cta_slots, emit=True, span=span, lookahead=la)
-                r = time_arm(arm, max(1, min(args.steps, 3)), 1, flush_buf)
+                k_runs = max(1, min(args.steps, 3))
+                with ClockSampler(torch.cuda.current_device()) as clk_row:   # clocks during each row too
+                    r = time_arm(arm, k_runs, 1, flush_buf)
                 ms = statistics.median(r["ms"])   # one host-side stall in a run cannot move it
                 study.append({"window": W, "span": span or W, "lookahead": effective_lookahead(W, span, la),
                               "release": span_mode, "ms_per_run": ms,
+                              "kernel_ms_per_run": r["stats"]["kernel_ms"] / max(1, r["stats"]["launches"]),
+                              "clocks": clk_row.summary(),
                               "tasks_per_s": (r["tasks"] / max(1, min(args.steps, 3))) / (ms / 1e3)})
                 arm.ctx.close()
         line["window_study"] = study
