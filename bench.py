@@ -95,7 +95,7 @@ def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: i
 # (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3789568, "sources_sha1": "ec69f06e747adb0d112e81447ddccad1a0abb302"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3718912, "sources_sha1": "561242431b13745b431b0b31ea568aaaa7c472be"}
 
 
 def kernel_sources_sha1() -> str:
