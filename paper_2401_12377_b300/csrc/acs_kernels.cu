@@ -125,7 +125,7 @@ __device__ __forceinline__ bool stopped(const KParams &P) { return ld_volatile_u
 //
 // Shared memory of a scheduler CTA (stream s):
 //   hist[H]     the descriptors of tasks seq mod H, copied in by the loader
-//               warp in batches of kPrefetch aligned to kPrefetch; it holds the
+//               warp in batches of up to kPrefetch; it holds the
 //               W - 1 predecessors of every task still to be checked
 //   pmask[H]    upstream-candidate mask of task seq mod H (bit i mod W for
 //               each conflicting predecessor i in [seq - W + 1, seq - 1])
@@ -436,9 +436,10 @@ __device__ void loader_warp(const KParams &P, uint32_t stream, uint8_t *smem_raw
             wait = true;
             host_wait = P.resident;                // idle until the host publishes work
         } else {
-            // a batch ends at a multiple of kPrefetch (so never across the
-            // device ring's end) or at the stream's end
-            const uint32_t nb = min((uint32_t)kPrefetch - (load_upto & (kPrefetch - 1u)), end - load_upto);
+            // a batch of up to kPrefetch stops at the stream's end and at the
+            // device ring's end (the first 16 descriptors an emitter publishes
+            // arrive in one batch, whatever their position)
+            const uint32_t nb = min(min((uint32_t)kPrefetch, end - load_upto), C - (load_upto & (C - 1u)));
             const uint32_t bhi = load_upto + nb;
             const uint32_t nx = lds_volatile(&S.sh->next);
             if (bhi + W > nx + H + 1) {
