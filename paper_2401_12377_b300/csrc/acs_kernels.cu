@@ -637,7 +637,8 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
             st_release_cta_shared(&S.ptag[j & HM], j + 1u);   // after the aux word
             if (tracing) check_cycles += clock64() - tc0;
         }
-        __syncwarp();
+        // no warp barrier here: the other lanes go on to the next task's
+        // loads and tests while lane 0 publishes (the next ballots reconverge)
     }
     if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
 }
