@@ -561,13 +561,20 @@ __device__ void checker_warp(const KParams &P, uint32_t stream, uint8_t *smem_ra
     unsigned long long check_cycles = 0;
     const bool tracing = (P.flags & ACS_FLAG_TRACE) != 0;
     const bool logging = (P.flags & ACS_FLAG_LOG) != 0;
+    // the loader's and the scheduler warp's progress as last read: both only
+    // grow, so while they cover a task no new read is needed (the acquire that
+    // returned cu_seen ordered every record below it); until the first read,
+    // values that cover nothing
+    uint32_t cu_seen = first, nx_seen = first - H;
     for (uint32_t j = first + w; open || j < end; j += kCheckers) {
         // wait: record j loaded and pmask slot j mod H consumed (j < next + H)
         uint32_t spins = 0, backoff = 32;
-        while (true) {
+        while (!((int32_t)(cu_seen - j) > 0 && (int32_t)(j - (nx_seen + H)) < 0)) {
             // an acquire load: the loader released the records below it
             const uint32_t cu = ld_acquire_cta_shared(&S.sh->complete_upto);
             const uint32_t nx = lds_volatile(&S.sh->next);
+            cu_seen = cu;
+            nx_seen = nx;
             if (cu > j && j < nx + H) break;
             if (lds_volatile(&S.sh->quit)) {
                 if (lane == 0 && check_cycles) atomicAdd(&P.sched_stats[stream].check_cycles, check_cycles);
