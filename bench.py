@@ -95,7 +95,7 @@ def effective_lookahead(window: int, span: int = 0, requested=None, n_streams: i
 # (else traffic is null).
 KERNEL_SOURCES = ("paper_2401_12377_b300/csrc/acs_kernels.cu", "paper_2401_12377_b300/csrc/acs_bodies.cuh",
                   "paper_2401_12377_b300/csrc/acs_internal.h")
-TRAFFIC_RLSIM = {"bytes_per_launch": 3718912, "sources_sha1": "561242431b13745b431b0b31ea568aaaa7c472be"}
+TRAFFIC_RLSIM = {"bytes_per_launch": 3698176, "sources_sha1": "6a70a08a9d4e3f0cfc1029c5fc521386a49e70b3"}
 
 
 def kernel_sources_sha1() -> str:
