@@ -507,11 +507,13 @@ def test_unlogged_windows_past_32_match_the_oracle(W):
 @pytest.mark.parametrize("W,L", [(32, None), (8, None), (33, 0), (64, 0)])
 def test_a_restarted_stream_keeps_the_window_dag_and_outputs(W, L):
     """One context runs the same stream from several positions: 0, just below the
-    2^31 limit, 0 again and a position that is no multiple of the window. Each run
-    finds ring slots, done words and log entries of the previous numbering; the
-    logged masks (by slot, seq mod W) decode to the oracle's D_W, every start is
-    legal against E and the outputs equal the oracle's. Past the limit a
-    submission is refused, and a stream that is not idle cannot be restarted."""
+    2^31 limit, 0 again and a position that is no multiple of the window, each in
+    two flushes (the second launch has only 10 tasks of the stream behind it since
+    the restart). Each run finds ring slots, done words and log entries of the
+    previous numbering; the logged masks (by slot, seq mod W) decode to the
+    oracle's D_W, every start is legal against E and the outputs equal the
+    oracle's. Past the limit a submission is refused, and a stream that is not
+    idle cannot be restarted."""
     s = sg.elementwise_stream(21, n_tasks=300, ranges=True)
     s.window = W
     E, D = oracle_dags(s)
@@ -523,9 +525,12 @@ def test_a_restarted_stream_keeps_the_window_dag_and_outputs(W, L):
             assert ctx.tail(0) == pos
             bufs = harness.DeviceBuffers(s.buffers)
             ids, packed = harness.pack_tasks(s.tasks, bufs)
-            ctx.submit_packed(ids, packed)
-            ctx.flush()
-            ctx.sync()
+            # two flushes: the second launch starts with only 10 tasks of the
+            # stream behind it since the restart (fewer than its W - 1 candidates)
+            for a, b in ((0, 10), (10, len(ids))):
+                ctx.submit_packed(ids[a:b], packed[a:b])
+                ctx.flush()
+                ctx.sync()
             masks, start, retire = ctx.log(0, pos, len(ids))
             rot = [sum(1 << ((b - pos) % W) for b in range(64) if (int(m) >> b) & 1) for m in masks]
             check_log(rot, start, retire, E, D, W)
