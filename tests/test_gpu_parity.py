@@ -545,3 +545,25 @@ def test_a_restarted_stream_keeps_the_window_dag_and_outputs(W, L):
         ctx.sync()
         ctx.rebase(0, 0)
         assert ctx.tail(0) == 0
+
+
+def test_emit_driver_restarts_a_long_stream_between_runs():
+    """A rigid-sphere stream placed just below harness.REBASE_AT runs across it;
+    before its next run the emit driver restarts the stream's positions at 0
+    (acs_stream_rebase). Both runs give the oracle's outputs, and the second
+    starts at position 0."""
+    p = sg.RLParams(n_env=64, steps=6)
+    _, o_bufs, _ = execute.run_rlsim(sg.RLSim(4, sg.RLParams(n_env=64, steps=6)), emit=True)
+    with harness.Context(32, capacity=1 << 14) as ctx:
+        ctx.rebase(0, harness.REBASE_AT - 200)
+        for run in range(2):
+            sim = sg.RLSim(4, p)
+            bufs = harness.DeviceBuffers(sim.buffers(emit=True))
+            drv = harness.RLEmitDriver(sim, bufs, ctx)
+            n = drv.run()
+            assert n > 200
+            if run == 0:
+                assert ctx.tail(0) == harness.REBASE_AT - 200 + n   # the first run crossed REBASE_AT
+            else:
+                assert ctx.tail(0) == n                             # the second started at 0
+            assert_same(bufs.download(), o_bufs, f"run {run}")
