@@ -194,6 +194,19 @@ class Server:
         self._cfg_stage = torch.empty((1024, 64), dtype=torch.uint8).pin_memory()
         self._head = np.zeros(self.slots, np.uint32)
         self._idle = np.zeros(self.slots, np.uint32)
+        self._tail_max = max(ctx.tail(s) for s in range(self.slots))   # highest slot position
+        self.restarts = 0
+
+    def _restart_positions(self) -> None:
+        """With no request in the system: end the resident launch, restart
+        every slot's positions at 0 (acs_stream_rebase; the library takes
+        host-submitted tasks only below 2^31 per stream) and start it again."""
+        self.ctx.stop()
+        for s in range(self.slots):
+            self.ctx.rebase(s)
+        self.ctx.start()
+        self._tail_max = 0
+        self.restarts += 1
 
     def run(self, arrivals: np.ndarray, kinds: np.ndarray, keep: Optional[set] = None,
             stall_s: float = 30.0) -> dict:
@@ -243,7 +256,9 @@ class Server:
                         continue                  # idle end still before the request's end
                     t = time.perf_counter()
                     lat[L.idx] = t - (t0 + float(arrivals[L.idx]))
-                    tasks[L.idx] = ctx.tail(s) - L.start
+                    tail = ctx.tail(s)
+                    tasks[L.idx] = tail - L.start
+                    self._tail_max = max(self._tail_max, tail)
                     if self.readback:
                         for name, (o, nb, dt) in L.entry.results.items():
                             if self._ring_pos + nb > self._ring.numel():
@@ -263,6 +278,9 @@ class Server:
                     free.append(s)
                     done += 1
                     last_done = last_move = t
+            # a slot past harness.REBASE_AT: restart the positions while nothing is in flight
+            if not live and not waiting and self._tail_max >= harness.REBASE_AT:
+                self._restart_positions()
             # admissions, oldest first
             batch = []
             for i, s in admit_fifo(waiting, free, in_use, self.budget,

@@ -75,3 +75,26 @@ def test_budget_limits_memory_in_use(cat):
     assert r["peak_bytes"] <= budget
     assert (r["latency_s"] > 0).all()
     assert r["queue_s"].max() > 0            # some requests waited for memory
+
+
+def test_server_restarts_slot_positions_when_idle(cat):
+    """Every slot starts 300 positions below harness.REBASE_AT; once a slot is
+    past it and no request is in flight, the server ends the resident launch,
+    restarts the slots' positions at 0 and starts it again. Every request still
+    completes with the oracle's results."""
+    n = 40
+    arrivals, kinds = sg.poisson_arrivals(5, n, 200.0, len(cat.specs))
+    with harness.Context(32, n_streams=4, resident=True, capacity=1 << 12) as ctx:
+        ctx.stop()
+        for s in range(4):
+            ctx.rebase(s, harness.REBASE_AT - 300)
+        ctx.start()
+        srv = serving.Server(cat, ctx)
+        r = srv.run(arrivals, kinds, keep=set(range(n)))
+        assert srv.restarts >= 1
+        assert max(ctx.tail(s) for s in range(4)) < harness.REBASE_AT
+        ctx.stop()
+    assert r["tasks"].min() > 0
+    for i in range(n):
+        k = int(kinds[i])
+        _close(r["results"][i], _oracle(cat, k), exact=cat.specs[k].kind == "rl")
