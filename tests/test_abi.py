@@ -204,3 +204,20 @@ def test_stream_rebase_checks_need_no_device(lib):
     assert re.search(r"#define ACS_ERR_RANGE\s+\(-8\)", hdr) and acs.ACS_ERR_RANGE == -8
     assert re.search(r"#define ACS_MAX_POSITION 0x80000000u", hdr) and acs.ACS_MAX_POSITION == 1 << 31
     assert b"2^31" in lib.acs_strerror(acs.ACS_ERR_RANGE)
+
+
+def test_header_compiles_as_c99(tmp_path):
+    """include/acs.h is a C header: it compiles on its own as C99 with every
+    warning enabled (no C++-only constructs, no missing includes)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_acs.c"
+    src.write_text('#include "acs.h"\n'
+                   'int main(void) { acs_config cfg; acs_config_default(&cfg);\n'
+                   '  return (int)cfg.lookahead == 0 ? ACS_ERR_RANGE : (int)(ACS_MAX_POSITION >> 31); }\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use_acs.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
