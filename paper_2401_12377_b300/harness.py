@@ -124,7 +124,8 @@ MODES = {"window": acs.ACS_MODE_WINDOW, "inorder": acs.ACS_MODE_INORDER, "graph"
          "sw": acs.ACS_MODE_SW}
 
 
-# Dispatch lookahead for Contexts created without one (None: the library's default).
+# Dispatch lookahead for window-mode Contexts (no free-slot span) created
+# without one (None: the library's default).
 DEFAULT_LOOKAHEAD: Optional[int] = None
 # a driver restarts an idle stream's positions once they pass this (the library
 # takes host-submitted tasks only below 2^31 per stream)
@@ -153,7 +154,7 @@ class Context:
         cfg.idle_limit_ms = idle_limit_ms
         cfg.sw_threads = sw_threads
         cfg.span = span
-        if lookahead is None:
+        if lookahead is None and mode == "window" and not span:
             lookahead = DEFAULT_LOOKAHEAD
         if lookahead is not None:          # None: the library's default (dispatch ahead, auto)
             cfg.lookahead = lookahead
