@@ -1167,7 +1167,8 @@ def bench_batched(args, torch, dist, world, rank, peaks, peak_src, flush_buf):
                          "note": "bytes named by the tasks' read+write segments per launch / mean launch time"},
             "sched_cycles_per_task": st["sched_cycles"] / max(1, st["sched_inserts"]),
             "gpu_launches": 1, "gpu_launches_note": "one resident persistent launch runs through the timed region",
-            "single_flush": {"ms_per_step": statistics.mean(res1["ms"]),
+            "pass_ms": [round(x, 3) for x in res["ms"]],
+            "single_flush": {"ms_per_step": statistics.mean(res1["ms"]), "pass_ms": [round(x, 3) for x in res1["ms"]],
                              "tasks_per_s": (res1["tasks"] / max(1, min(args.steps, 3))) / (statistics.mean(res1["ms"]) / 1e3),
                              "kernel_ms_per_step": avg_launch_s * 1e3,
                              "note": "all streams submitted, then one flush and one launch per pass"},
@@ -1340,7 +1341,7 @@ SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "stream
             "latency_ms", "queue_wait_ms", "latency_breakdown", "offered_tasks_per_s", "requests_per_s",
             "mean_in_flight", "roofline", "critical_path", "cpu_baseline", "e2e", "speedup_vs_inorder",
             "speedup_vs_graph_with_build", "speedup_vs_graph_launch_only", "speedup_vs_sw_host_scheduler",
-            "inorder", "graph_with_build", "graph_launch", "sw_host_scheduler", "single_flush", "autotune",
+            "inorder", "graph_with_build", "graph_launch", "sw_host_scheduler", "single_flush", "pass_ms", "autotune",
             "resident_per_input", "gpu_launches", "gpu_launches_per_step", "clocks")
 
 
