@@ -496,6 +496,44 @@ def critical_path(ctx, stream: int, first: int, n: int):
     return (float(fin[k]), int(cnt[k])) if n else (0.0, 0)
 
 
+def window_bound(ctx, first: int, n: int, window: int, emitter) -> dict:
+    """Makespan of an as-soon-as-possible schedule of a logged, traced stream
+    under the window rule with no scheduling overhead: a task starts once its
+    logged conflicting predecessors and every task `window` or more positions
+    back have ended (a window holds `window` tasks), and an emitted task once
+    its emit task has started (optimistic) or ended. Tasks take their traced
+    body times. emitter[j] is the position of the emit task that appended
+    task j, or -1. Returns the two makespans in microseconds."""
+    span = ctx.span
+    masks, _, _ = ctx.log(0, first, n)
+    tr = ctx.trace(0, first, n).astype(np.int64)
+    body = np.maximum(tr[:, 3] - tr[:, 2], 0) / 1e3
+    preds = []
+    for j in range(n):
+        m, seq, p = int(masks[j]), first + j, []
+        while m:
+            b = (m & -m).bit_length() - 1
+            m &= m - 1
+            i = j - (seq - b) % span
+            if 0 <= i < j:
+                p.append(i)
+        preds.append(p)
+    out = {}
+    for release in ("start", "end"):
+        S, E, runmax = np.zeros(n), np.zeros(n), np.zeros(n)
+        for j in range(n):
+            t = max((E[i] for i in preds[j]), default=0.0)
+            if j >= window:
+                t = max(t, runmax[j - window])
+            e = emitter[j]
+            if e >= 0:
+                t = max(t, S[e] if release == "start" else E[e])
+            S[j], E[j] = t, t + body[j]
+            runmax[j] = max(runmax[j - 1] if j else 0.0, E[j])
+        out[release] = float(E.max()) if n else 0.0
+    return out
+
+
 def task_segments(rows):
     """Read and write segments of packed task rows, as the library resolves
     them (acs_get_addresses)."""
@@ -1484,6 +1522,31 @@ def main():
                              "note": "longest chain of the full dependency DAG of the stream's host-driven "
                                      "form (no emit tasks), tasks weighted by their body times in a traced "
                                      "run: the makespan with no scheduling overhead"}
+
+    # ---- the window's bound: the same stream with device emission, traced -------------------
+    # (the emit task of a step follows the step's tasks in the host-driven plans)
+    kinds = []
+    for i, pl in enumerate(plans):
+        kinds += [0] * len(pl.kind) + ([1] if i < len(plans) - 1 else [])
+    tw = RLBench("window", seed, args.window, args.cta_slots, emit=True, traced=True)
+    for _ in range(2):
+        tw.reset_device()
+        n_w = tw.run_once()
+    if n_w == len(kinds):
+        emitter, last = [], -1
+        for j, k in enumerate(kinds):
+            emitter.append(last)
+            if k:
+                last = j
+        wb = window_bound(tw.ctx, tw.ctx.tail(0) - n_w, n_w, args.window, emitter)
+        line["window_bound"] = {
+            "us": [wb["start"], wb["end"]], "kernel_us_per_run": avg_launch_s * 1e6,
+            "frac": [wb["start"] / (avg_launch_s * 1e6), wb["end"] / (avg_launch_s * 1e6)],
+            "note": "as-soon-as-possible schedule of the emitted stream with no scheduling overhead: a task "
+                    "starts once its logged conflicting predecessors and every task window or more "
+                    "positions back have ended, an emitted task once its emit task started (first value) "
+                    "or ended (second); traced body times"}
+    tw.ctx.close()
 
     # ---- baselines on the same box -----------------------------------------------------------
     if not args.no_baselines:

@@ -65,6 +65,22 @@ def test_critical_path_of_a_logged_dag(first):
     assert bench.critical_path(ctx, 0, first, 6) == (5.0, 1)
 
 
+@pytest.mark.parametrize("first", [0, 5])
+def test_window_bound_of_a_logged_stream(first):
+    import bench
+    # no conflicts, window 2: task j waits for every task j - 2 or further back
+    # to end; bodies 1, 2, 3, 4 us give ends 1, 2, 4, 6
+    ctx = _FakeCtx(8, first, [], [1, 2, 3, 4])
+    assert bench.window_bound(ctx, first, 4, 2, [-1] * 4) == {"start": 6.0, "end": 6.0}
+    # a wide window: the chain 0 -> 1 -> 2 (1 + 2 + 3 us) binds, task 3 runs beside it
+    ctx = _FakeCtx(8, first, [(0, 1), (1, 2)], [1, 2, 3, 1])
+    assert bench.window_bound(ctx, first, 4, 8, [-1] * 4) == {"start": 6.0, "end": 6.0}
+    # tasks 1 and 2 appended by the emit task 0 (2 us): released at its start
+    # they end at 1 us and the emit binds (2 us); at its end, 2 + 1 us
+    ctx = _FakeCtx(8, first, [], [2, 1, 1])
+    assert bench.window_bound(ctx, first, 3, 8, [-1, 0, 0]) == {"start": 2.0, "end": 3.0}
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_full_dag_critical_path_against_brute_force(seed):
     """bench.critical_path_full (per-byte last writer / readers) against the
