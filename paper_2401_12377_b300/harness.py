@@ -185,7 +185,12 @@ class Context:
         cfg.cuda_stream = C.c_void_p(cuda_stream)
         self.window, self.mode, self.n_streams = window, mode, n_streams
         self.span = span or window   # ring span: logged masks are over span - 1 predecessors
-        self.h = acs.acs_init(window, cfg)
+        try:
+            self.h = acs.acs_init(window, cfg)
+        except acs.AcsError:
+            if self._prev_stream is not None:     # leave torch's current stream as it was
+                torch.cuda.set_stream(self._prev_stream)
+            raise
         self.resident = False
         if resident:
             self.start()

@@ -271,3 +271,18 @@ def test_a_smaller_context_does_not_break_a_larger_one():
         ref = execute.run_inorder(s.buffers, s.tasks)
         out = bufs2.download()
         assert all(np.array_equal(out[k], ref[k]) for k in ref)
+
+
+def test_default_lookahead_reaches_window_mode_contexts_only(monkeypatch):
+    """A process-wide default lookahead (bench.py --lookahead) applies to
+    window-mode contexts without a free-slot span; the host-scheduler,
+    in-order and graph modes and span contexts, which take none, still open."""
+    monkeypatch.setattr(harness, "DEFAULT_LOOKAHEAD", 8)
+    for mode in ("window", "inorder", "graph", "sw"):
+        with harness.Context(8, mode=mode) as ctx:
+            assert ctx.mode == mode
+    with harness.Context(8, span=32) as ctx:
+        assert ctx.span == 32
+    # an explicit lookahead on a mode that takes none is still refused
+    with pytest.raises(acs.AcsError):
+        harness.Context(8, mode="sw", lookahead=8)
